@@ -1,0 +1,286 @@
+"""Throughput of the Enskog-Vlasov lattice Boltzmann step on GB300.
+
+Workload (N = 1, per GPU): the 2-D static-droplet Laplace sweep -- nine
+independent 1024 x 1024 periodic D2Q9 layers (T/Tc in {0.7, 0.8, 0.9} x droplet
+radius in {64, 128, 256}, tanh interface of width 4, u = 0), thermal double
+population, FP32 storage and arithmetic, Carnahan-Starling Enskog pressure with
+b = 4, a = 0.1, kappa = 0.116 (10-90 % width 4 at T/Tc = 0.7), bare tau = 0.3, lambda = 1.  One step = one
+lattice update of all nine layers (9 x 2^20 lattice updates).  The populations
+(1.36 GB per step read + written) exceed the 129 MB L2, so no flush is needed.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (the
+reference arm), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 1024
+TRS = (0.7, 0.8, 0.9)
+RADII = (64.0, 128.0, 256.0)
+A, B, KAPPA, TAU = 0.1, 4.0, 0.116, 0.3
+BYTES_PER_LU = 2 * 9 * 2 * 4          # D2Q9, f and g, read + write, FP32
+WORKLOAD = "droplet Laplace sweep: 9 x 1024^2 D2Q9 thermal, FP32"
+
+
+def workload_fields(coexistence, critical_point, layers=None):
+    """Initial fields of the sweep (rho, u, T) stacked along z."""
+    from paper_2508_00577_gb300 import inputs
+    _, Tc = critical_point(1, A, B)
+    cases = []
+    for tr in TRS:
+        rv, rl = coexistence(1, A, B, tr * Tc)
+        for R in RADII:
+            cases.append((R, rv, rl, tr * Tc))
+    if layers is not None:
+        cases = [cases[k] for k in layers]
+    return inputs.droplet_stack(NX, NY, cases), len(cases)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"evlbm_clocks_{os.getpid()}.csv")
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            try:
+                with open(self.path) as fh:
+                    self.lines = [l for l in fh.read().splitlines() if l.strip()]
+                os.remove(self.path)
+            except OSError:
+                self.lines = []
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(self.NAMES, parts[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(steps=None, budget_s=15.0):
+    """The FP64 oracle on one 1024^2 layer of the workload (T/Tc = 0.8, R = 128)."""
+    import oracle
+    import oracle.eos as E
+    (rho, u, T), _ = workload_fields(E.maxwell, E.critical_point, layers=[4])
+    p = oracle.Params(Q=9, nx=NX, ny=NY, nz=1, eos=1, a=A, b=B, kappa=KAPPA, tau=TAU, thermal=1)
+    s = oracle.State(p, rho, u, T)
+    s.step(1)                                    # warm-up (page in, thread pool)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        s.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n >= steps) or (steps is None and el >= budget_s):
+            break
+    mlups = NX * NY * n / el / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one 1024^2 layer (T/Tc=0.8, R=128) of the sweep, {n} steps, {el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import oracle.eos as E
+    (rho, u, T), _ = workload_fields(E.maxwell, E.critical_point, layers=[4])
+    p = oracle.Params(Q=9, nx=NX, ny=NY, nz=1, eos=1, a=A, b=B, kappa=KAPPA, tau=TAU, thermal=1)
+    s = oracle.State(p, rho, u, T)
+    for _ in range(args.warmup):
+        s.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(1)
+    el = time.perf_counter() - t0
+    mlups = NX * NY * args.steps / el / 1e6
+    sample = f"one 1024^2 layer (T/Tc=0.8, R=128) of the sweep per step, {args.steps} steps"
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run(args):
+    import torch
+
+    import paper_2508_00577_gb300 as ev
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+
+    layers = list(range(args.layers)) if args.layers < 9 else None
+    (rho, u, T), nz = workload_fields(ev.lbm_coexistence, ev.lbm_critical_point, layers=layers)
+    params = ev.lbm_params.make(lattice=ev.LBM_D2Q9, nx=NX, ny=NY, nz=nz, eos=ev.LBM_EOS_CS, a=A, b=B,
+                                kappa=KAPPA, tau=TAU, lambda_=1.0, thermal=1, precision=ev.LBM_FP32)
+    N = params.N
+    lat = ev.Lattice(params, rho, u, T, stream=stream.cuda_stream)
+    launches_per_step = ev.lbm_launches_per_step(lat.ctx)
+
+    # Warm-up
+    lat.step(args.warmup)
+    torch.cuda.synchronize(dev)
+
+    # Timed region: one event pair per step on the library's stream.
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            starts[k].record(stream)
+            lat.step(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    per_step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(per_step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * N * args.steps / (total_ms * 1e-3) / 1e6
+
+    ok = np.isfinite(lat.conserved()).all()
+    lat.close()
+
+    # End to end through the public API with host buffers: init (H2D) + steps + moments (D2H).
+    e2e_steps = args.steps
+    pinned = [torch.from_numpy(a).pin_memory().numpy() for a in (rho, u.reshape(-1), T)]
+    out_rho = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    with ev.Lattice(params, pinned[0], pinned[1], pinned[2], stream=stream.cuda_stream) as lat2:
+        lat2.step(e2e_steps)
+        ev.lbm_moments(lat2.ctx, out_rho, None, None, None)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": N * e2e_steps / e2e_s / 1e6 * world, "unit": "MLUPS",
+           "h2d_bytes_per_step": int(sum(a.nbytes for a in pinned) / e2e_steps),
+           "d2h_bytes_per_step": int(out_rho.nbytes / e2e_steps),
+           "what": f"lbm_init from host fields + {e2e_steps} x lbm_step + lbm_moments(rho) to host"}
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_LU * N / (ms_per_step * 1e-3) / 1e9
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if nz == 9 else f"{nz} of the 9 layers of: {WORKLOAD}", "nodes_per_gpu": N, "layers": nz, "lattice": "D2Q9",
+                   "thermal": True, "precision": "fp32", "l2": "inputs larger than L2 (1.36 GB/step)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "note": f"{BYTES_PER_LU} algorithmic B/LU; peak {peak_kind} copy bandwidth"},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "finite": bool(ok),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--layers", type=int, default=9, help="layers of the sweep (9 = the full workload)")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

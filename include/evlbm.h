@@ -1,0 +1,155 @@
+/*
+ * evlbm.h -- C ABI of the GB300 Enskog-Vlasov lattice Boltzmann library.
+ *
+ * The library advances the explicit lattice Boltzmann model of Karlin &
+ * Hosseini, "Practical Kinetic Models for Dense Fluids" (arXiv 2508.00577):
+ * one time step is
+ *   pull streaming -> raw moments (rho, j, Gamma) -> non-local force F in the
+ *   Enskog gauge P0 = P_E -> shifted velocity u and energy E -> EOS (P0,
+ *   gamma0) -> gradient corrections (Phi, Phi', q') -> equilibria f^eq, f*,
+ *   g^eq, g* -> BGK-type collision,
+ * following Eqs. (pre_LBM), (beta), (u_shift), (T_shift), (EVforce1), (Ework),
+ * (P0E), (phi), (feq), (f_star), (correction_u), (correction_gamma), (gamma),
+ * (geq), (gstar), (g_corr), (correction_q) of the paper.
+ *
+ * Conventions shared by every entry point
+ *   - Lattice units: dt = 1, lattice spacing 1, periodic boundaries.
+ *   - Lattice LBM_D2Q9 is the c_z-marginal of the paper's D3Q27 (3-D
+ *     thermodynamics, rho E = 3/2 rho RT + 1/2 rho u^2).  A D2Q9 lattice with
+ *     nz > 1 is a stack of nz independent 2-D layers.
+ *   - Fields are structure-of-arrays with x fastest: node n = x + nx*(y + ny*z),
+ *     N = nx*ny*nz.  Vector fields are [D][N] (D = 2 for D2Q9, 3 for D3Q27).
+ *     Populations are [Q][N] with i = (cx+1) + 3(cy+1) + 9(cz+1).
+ *   - Every function returns LBM_OK (0) or a negative LBM_E* code.  Errors on
+ *     a context are described by lbm_last_error(ctx).  Invalid arguments never
+ *     reach the GPU.
+ *   - The context owns every device buffer it allocates; the caller owns every
+ *     pointer it passes in and may free it as soon as the call returns.
+ *   - Work is enqueued on the context's stream (the cudaStream_t handle passed
+ *     to lbm_init as void*; NULL = the legacy default stream).  Calls that
+ *     return host data synchronise that stream.
+ */
+#ifndef EVLBM_H
+#define EVLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_EINVAL (-1)      /* invalid argument */
+#define LBM_ECUDA (-2)       /* a CUDA runtime call failed */
+#define LBM_ENOMEM (-3)      /* device or host allocation failed */
+#define LBM_ENONFINITE (-4)  /* a NaN or Inf was found in the state */
+#define LBM_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
+
+#define LBM_D2Q9 0
+#define LBM_D3Q27 1
+
+#define LBM_EOS_VDW 0        /* P_E = rho RT / (1 - b rho)  (the paper's form) */
+#define LBM_EOS_CS 1         /* Carnahan-Starling contact value, eta = b rho / 4 */
+
+#define LBM_FP64 0           /* FP64 storage and arithmetic (bit-exact reference order) */
+#define LBM_FP32 1           /* FP32 storage and arithmetic */
+#define LBM_FP16_DEV 2       /* FP16 storage of f_i - w_i rho_ref, g_i - w_i rho_ref E_ref; FP32 arithmetic */
+#define LBM_BF16_DEV 3       /* BF16 storage of the same deviations; FP32 arithmetic */
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Model and lattice parameters.  The paper fixes the lattice (D3Q27), the
+ * Enskog pressure P_E = rho RT/(1 - b rho), the Vlasov pressure P_V = -a rho^2
+ * with capillarity kappa (Enskog-Vlasov closure, Eqs. EVforce1, Ework), the
+ * bare relaxation time tau with beta = dt/(2 tau + dt) (Eq. beta) and the
+ * relaxation time lambda of the shifted equilibrium (lambda = dt in the paper). */
+typedef struct {
+    int lattice;        /* LBM_D2Q9 or LBM_D3Q27 */
+    int nx, ny, nz;     /* lattice size, each >= 1; nz = 1 for a single 2-D layer */
+    int eos;            /* LBM_EOS_VDW or LBM_EOS_CS */
+    double a;           /* Vlasov attraction a >= 0 */
+    double b;           /* excluded volume b >= 0 */
+    double R;           /* gas constant R > 0 (T in the API, RT inside) */
+    double kappa;       /* capillarity coefficient kappa >= 0 */
+    double tau;         /* BARE relaxation time tau > 0 (Eq. beta) */
+    double lambda;      /* lambda > 0 (1.0 = dt as in the paper) */
+    int thermal;        /* 1: f and g double population (energy equation);
+                           0: temperature frozen at the initial field, g absent */
+    int precision;      /* LBM_FP64, LBM_FP32, LBM_FP16_DEV or LBM_BF16_DEV */
+    int force_form;     /* 0: divergence (Korteweg stress) form of F (conserves momentum);
+                           1: literal grad(a rho^2) + kappa rho grad(lap rho) */
+} lbm_params;
+
+/* Create a context and the initial state from HOST fields (FP64):
+ *   rho[N], u[D][N], T[N] (temperature; RT = R T).
+ * The populations start at f = f^eq(rho, u, P0/rho) and g = g^eq(rho, u, RT)
+ * (Eqs. feq, geq), so the raw momentum is rho u and the first step sees the
+ * shifted velocity u + F/(2 rho) (Eq. u_shift).
+ * `stream` is a cudaStream_t (or NULL).  On success *out receives the context.
+ * Errors: LBM_EINVAL (bad parameters or pointers), LBM_ENOMEM, LBM_ECUDA,
+ * LBM_ENONFINITE (non-finite or non-positive rho, non-positive T). */
+int lbm_init(const lbm_params *params, const double *rho, const double *u, const double *T,
+             void *stream, lbm_ctx **out);
+
+/* Advance the state by n_steps >= 0 time steps (Eq. pre_LBM per step).
+ * Asynchronous on the context's stream.  Errors: LBM_EINVAL, LBM_ECUDA. */
+int lbm_step(lbm_ctx *ctx, int n_steps);
+
+/* Macroscopic fields of the current state, exactly as the next step computes
+ * them (streaming, raw moments, force, Eq. u_shift, energy): rho[N], u[D][N],
+ * T[N], F[D][N] into HOST arrays (FP64).  Any output may be NULL.  Q~ is zero
+ * in the Enskog gauge (Eq. P0E) and is not returned.  Synchronises the stream.
+ * Errors: LBM_EINVAL, LBM_ECUDA. */
+int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *T, double *F);
+
+/* The same fields as FP32 into DEVICE arrays the caller owns (e.g. torch
+ * tensors): d_rho[N], d_u[D][N], d_T[N]; any may be NULL.  Asynchronous on the
+ * context's stream.  Errors: LBM_EINVAL, LBM_ECUDA. */
+int lbm_moments_device(lbm_ctx *ctx, float *d_rho, float *d_u, float *d_T);
+
+/* Copy the current post-collision populations to HOST arrays f[Q][N] and
+ * g[Q][N] (g ignored and may be NULL when thermal = 0), converted to FP64
+ * (deviation storage is expanded).  Synchronises the stream. */
+int lbm_populations(lbm_ctx *ctx, double *f, double *g);
+
+/* Conserved totals of the current state in FP64, reduced on the GPU in a fixed
+ * order: out[0] = sum rho, out[1..3] = sum of the raw momentum (x, y, z; z = 0
+ * for D2Q9), out[4] = sum of the energy population (0 when thermal = 0).
+ * Returns LBM_ENONFINITE if any population is NaN or Inf.  Synchronises. */
+int lbm_conserved(lbm_ctx *ctx, double out[5]);
+
+/* Number of time steps taken since lbm_init. */
+long long lbm_step_count(const lbm_ctx *ctx);
+
+/* Number of kernel launches one lbm_step time step enqueues for this context
+ * (1 for the fused single-pass kernel, 4 for the stage-by-stage kernels);
+ * -1 for NULL. */
+int lbm_launches_per_step(const lbm_ctx *ctx);
+
+/* Wait for all work queued on the context's stream. */
+int lbm_sync(lbm_ctx *ctx);
+
+/* Release the context and its device memory.  NULL is accepted. */
+int lbm_free(lbm_ctx *ctx);
+
+/* Message describing the last error on ctx (owned by ctx; "" if none).
+ * lbm_last_error(NULL) describes the last failed lbm_init in this thread. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Liquid-vapour coexistence by the Maxwell construction (equal pressure and
+ * equal chemical potential of p = P_E - a rho^2, the line of the paper's
+ * Fig. 1), solved by Newton iteration in FP64 on the GPU (device 0 of the
+ * current context).  eos = LBM_EOS_VDW or LBM_EOS_CS; RT below the critical
+ * value.  out[0] = rho_vapour, out[1] = rho_liquid (host).
+ * Errors: LBM_EINVAL (RT >= RT_c or bad constants), LBM_ECUDA, LBM_ETIMEOUT
+ * (no convergence within the iteration limit). */
+int lbm_coexistence(int eos, double a, double b, double RT, double out[2]);
+
+/* Critical point (rho_c, RT_c) of p = P_E - a rho^2 (host computation). */
+int lbm_critical_point(int eos, double a, double b, double out[2]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EVLBM_H */

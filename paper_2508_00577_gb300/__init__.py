@@ -1,0 +1,258 @@
+"""GB300 Enskog-Vlasov lattice Boltzmann library (Karlin & Hosseini, arXiv 2508.00577).
+
+Thin Python binding of the C ABI declared in ``include/evlbm.h``: the functions
+below carry the C names and only marshal arguments; every step of the model
+runs in the CUDA kernels of ``libevlbm.so`` (built in-tree from ``csrc/``).
+There is no CPU fallback: if the shared library cannot be built or loaded,
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "lbm_params", "lib", "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_device",
+    "lbm_populations", "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_sync", "lbm_free",
+    "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "LBMError", "Lattice",
+    "LBM_D2Q9", "LBM_D3Q27", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
+    "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS",
+]
+
+LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENOMEM, LBM_ENONFINITE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5
+LBM_D2Q9, LBM_D3Q27 = 0, 1
+LBM_EOS_VDW, LBM_EOS_CS = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
+
+_ERRNAMES = {LBM_EINVAL: "LBM_EINVAL", LBM_ECUDA: "LBM_ECUDA", LBM_ENOMEM: "LBM_ENOMEM",
+             LBM_ENONFINITE: "LBM_ENONFINITE", LBM_ETIMEOUT: "LBM_ETIMEOUT"}
+
+# Every symbol include/evlbm.h declares.
+EXPORTED_SYMBOLS = (
+    "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_populations",
+    "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_sync", "lbm_free",
+    "lbm_last_error", "lbm_coexistence", "lbm_critical_point",
+)
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("eos", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("tau", ctypes.c_double), ("lambda_", ctypes.c_double),
+        ("thermal", ctypes.c_int), ("precision", ctypes.c_int), ("force_form", ctypes.c_int),
+    ]
+
+    @classmethod
+    def make(cls, lattice=LBM_D2Q9, nx=64, ny=64, nz=1, eos=LBM_EOS_CS, a=0.1, b=4.0, R=1.0,
+             kappa=0.0, tau=0.3, lambda_=1.0, thermal=1, precision=LBM_FP32, force_form=0):
+        return cls(lattice, nx, ny, nz, eos, a, b, R, kappa, tau, lambda_, thermal, precision, force_form)
+
+    @property
+    def Q(self):
+        return 9 if self.lattice == LBM_D2Q9 else 27
+
+    @property
+    def D(self):
+        return 2 if self.lattice == LBM_D2Q9 else 3
+
+    @property
+    def N(self):
+        return self.nx * self.ny * self.nz
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the in-tree CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import _build
+            path = _build.LIB
+            if not os.path.exists(path) or _build_needed(_build):
+                _build.build()
+            L = ctypes.CDLL(path)
+            dp = ctypes.POINTER(ctypes.c_double)
+            pp = ctypes.POINTER(lbm_params)
+            vp = ctypes.c_void_p
+            L.lbm_init.argtypes = [pp, dp, dp, dp, vp, ctypes.POINTER(vp)]
+            L.lbm_step.argtypes = [vp, ctypes.c_int]
+            L.lbm_moments.argtypes = [vp, dp, dp, dp, dp]
+            L.lbm_moments_device.argtypes = [vp, vp, vp, vp]
+            L.lbm_populations.argtypes = [vp, dp, dp]
+            L.lbm_conserved.argtypes = [vp, dp]
+            L.lbm_step_count.argtypes = [vp]
+            L.lbm_step_count.restype = ctypes.c_longlong
+            L.lbm_launches_per_step.argtypes = [vp]
+            L.lbm_sync.argtypes = [vp]
+            L.lbm_free.argtypes = [vp]
+            L.lbm_last_error.argtypes = [vp]
+            L.lbm_last_error.restype = ctypes.c_char_p
+            L.lbm_coexistence.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+            L.lbm_critical_point.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+            _lib = L
+    return _lib
+
+
+def _build_needed(b) -> bool:
+    try:
+        t = os.path.getmtime(b.LIB)
+    except OSError:
+        return True
+    for d in (b.CSRC, os.path.join(b.HERE, "..", "include")):
+        for f in os.listdir(d):
+            if os.path.getmtime(os.path.join(d, f)) > t:
+                return True
+    return False
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise TypeError("expected a C-contiguous float64 numpy array")
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc, ctx=None):
+    if rc != LBM_OK:
+        msg = lib().lbm_last_error(ctx)
+        raise LBMError(rc, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# C ABI, same names
+# ---------------------------------------------------------------------------
+
+def lbm_init(params: lbm_params, rho, u, T, stream=0):
+    """Context from host FP64 fields rho[N], u[D][N], T[N]; returns the opaque handle."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64).ravel()
+    u = np.ascontiguousarray(u, dtype=np.float64).ravel()
+    T = np.ascontiguousarray(T, dtype=np.float64).ravel()
+    if params.lattice in (LBM_D2Q9, LBM_D3Q27) and min(params.nx, params.ny, params.nz) >= 1:
+        N, D = params.N, params.D
+        if rho.size != N or T.size != N or u.size != D * N:
+            raise ValueError(f"fields must hold rho[{N}], u[{D}][{N}], T[{N}]")
+    out = ctypes.c_void_p()
+    rc = lib().lbm_init(ctypes.byref(params), _dptr(rho), _dptr(u), _dptr(T), ctypes.c_void_p(stream),
+                        ctypes.byref(out))
+    _check(rc, None)
+    return out.value
+
+
+def lbm_step(ctx, n_steps=1):
+    _check(lib().lbm_step(ctx, int(n_steps)), ctx)
+
+
+def lbm_moments(ctx, rho=None, u=None, T=None, F=None):
+    _check(lib().lbm_moments(ctx, _dptr(rho), _dptr(u), _dptr(T), _dptr(F)), ctx)
+
+
+def lbm_moments_device(ctx, d_rho=0, d_u=0, d_T=0):
+    """Device pointers (ints, e.g. tensor.data_ptr()) of FP32 outputs; 0 = skip."""
+    _check(lib().lbm_moments_device(ctx, ctypes.c_void_p(d_rho or None), ctypes.c_void_p(d_u or None),
+                                    ctypes.c_void_p(d_T or None)), ctx)
+
+
+def lbm_populations(ctx, f, g=None):
+    _check(lib().lbm_populations(ctx, _dptr(f), _dptr(g)), ctx)
+
+
+def lbm_conserved(ctx):
+    out = np.zeros(5)
+    _check(lib().lbm_conserved(ctx, _dptr(out)), ctx)
+    return out
+
+
+def lbm_step_count(ctx):
+    return lib().lbm_step_count(ctx)
+
+
+def lbm_launches_per_step(ctx):
+    return lib().lbm_launches_per_step(ctx)
+
+
+def lbm_sync(ctx):
+    _check(lib().lbm_sync(ctx), ctx)
+
+
+def lbm_free(ctx):
+    _check(lib().lbm_free(ctx), None)
+
+
+def lbm_last_error(ctx=None):
+    m = lib().lbm_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def lbm_coexistence(eos, a, b, RT):
+    out = np.zeros(2)
+    rc = lib().lbm_coexistence(int(eos), float(a), float(b), float(RT), _dptr(out))
+    if rc != LBM_OK:
+        raise LBMError(rc, "lbm_coexistence")
+    return float(out[0]), float(out[1])
+
+
+def lbm_critical_point(eos, a, b):
+    out = np.zeros(2)
+    rc = lib().lbm_critical_point(int(eos), float(a), float(b), _dptr(out))
+    if rc != LBM_OK:
+        raise LBMError(rc, "lbm_critical_point")
+    return float(out[0]), float(out[1])
+
+
+class Lattice:
+    """Convenience owner of one context (frees it on close)."""
+
+    def __init__(self, params: lbm_params, rho, u, T, stream=0):
+        self.params = params
+        self.ctx = lbm_init(params, rho, u, T, stream)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+        return self
+
+    def moments(self):
+        p = self.params
+        rho, u, T, F = np.zeros(p.N), np.zeros(p.D * p.N), np.zeros(p.N), np.zeros(p.D * p.N)
+        lbm_moments(self.ctx, rho, u, T, F)
+        return rho, u.reshape(p.D, p.N), T, F.reshape(p.D, p.N)
+
+    def populations(self):
+        p = self.params
+        f = np.zeros(p.Q * p.N)
+        g = np.zeros(p.Q * p.N) if p.thermal else None
+        lbm_populations(self.ctx, f, g)
+        return f.reshape(p.Q, p.N), (g.reshape(p.Q, p.N) if g is not None else None)
+
+    def conserved(self):
+        return lbm_conserved(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            lbm_free(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,409 @@
+// C ABI of the Enskog-Vlasov lattice Boltzmann library (declared in include/evlbm.h).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <vector>
+
+#include "../../include/evlbm.h"
+#include "dispatch.h"
+
+using evlbm::KParams;
+
+struct lbm_ctx {
+    lbm_params P;
+    KParams K;
+    cudaStream_t stream;
+    int Q, D;
+    long long N;
+    size_t pop_bytes;      // bytes per stored population
+    size_t real_bytes;     // bytes per scratch value (8 for FP64, 4 otherwise)
+    void *f[2], *g[2];
+    int cur;
+    void *RT_iso;          // frozen R*T field (thermal = 0), in the scratch precision
+    void *scratch;         // stage-kernel fields, allocated on first use
+    void *red;             // reduction work space
+    long long steps;
+    char err[512];
+};
+
+namespace {
+
+thread_local char g_init_err[512] = "";
+
+int fail(lbm_ctx *c, int code, const char *fmt, ...)
+{
+    char *dst = c ? c->err : g_init_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(lbm_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                               \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);  \
+    } while (0)
+
+bool fp64(const lbm_ctx *c) { return c->P.precision == LBM_FP64; }
+
+int ensure_scratch(lbm_ctx *c)
+{
+    if (c->scratch) return LBM_OK;
+    CK(c, cudaMalloc(&c->scratch, c->real_bytes * evlbm::kRefFieldCount * (size_t)c->N));
+    return LBM_OK;
+}
+
+int validate(const lbm_params *p)
+{
+    if (!p) return fail(nullptr, LBM_EINVAL, "params is NULL");
+    if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q27) return fail(nullptr, LBM_EINVAL, "lattice must be 0 or 1");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(nullptr, LBM_EINVAL, "lattice sizes must be >= 1");
+    if ((long long)p->nx * p->ny * p->nz > (1LL << 31) - 1)
+        return fail(nullptr, LBM_EINVAL, "more than 2^31-1 nodes");
+    if (p->eos != LBM_EOS_VDW && p->eos != LBM_EOS_CS) return fail(nullptr, LBM_EINVAL, "eos must be 0 or 1");
+    if (!(p->a >= 0.0) || !(p->b >= 0.0) || !(p->kappa >= 0.0) || !(p->R > 0.0))
+        return fail(nullptr, LBM_EINVAL, "a, b, kappa must be >= 0 and R > 0");
+    if (!(p->tau > 0.0) || !(p->lambda > 0.0)) return fail(nullptr, LBM_EINVAL, "tau and lambda must be > 0");
+    if (p->thermal != 0 && p->thermal != 1) return fail(nullptr, LBM_EINVAL, "thermal must be 0 or 1");
+    if (p->precision < LBM_FP64 || p->precision > LBM_BF16_DEV)
+        return fail(nullptr, LBM_EINVAL, "precision must be 0..3");
+    if (p->force_form != 0 && p->force_form != 1) return fail(nullptr, LBM_EINVAL, "force_form must be 0 or 1");
+    return LBM_OK;
+}
+
+// Fills the kernel parameter block; rho_ref/E_ref are the deviation references.
+void fill_kparams(lbm_ctx *c, double rho_ref, double E_ref)
+{
+    const lbm_params &p = c->P;
+    KParams &k = c->K;
+    memset(&k, 0, sizeof(k));
+    k.nx = p.nx;
+    k.ny = p.ny;
+    k.nz = p.nz;
+    k.N = c->N;
+    k.eos = p.eos;
+    k.thermal = p.thermal;
+    k.force_form = p.force_form;
+    k.a = p.a;
+    k.b = p.b;
+    k.kappa = p.kappa;
+    k.lambda = p.lambda;
+    const double beta = 1.0 / (2.0 * p.tau + 1.0);   // Eq. (beta), dt = 1
+    k.c_eq = 2.0 * beta;
+    k.c_star = (1.0 / p.lambda) * (1.0 - beta);      // (dt/lambda)(1 - beta)
+    k.rho_ref = rho_ref;
+    k.E_ref = E_ref;
+    const bool dev = p.precision == LBM_FP16_DEV || p.precision == LBM_BF16_DEV;
+    for (int i = 0; i < c->Q; ++i) {
+        const double w = evlbm::w_of(i, c->Q);
+        k.foff[i] = dev ? float(w * rho_ref) : 0.0f;
+        k.goff[i] = dev ? float(w * rho_ref * E_ref) : 0.0f;
+    }
+}
+
+int run_macro(lbm_ctx *c)
+{
+    int rc = ensure_scratch(c);
+    if (rc) return rc;
+    cudaError_t e = fp64(c) ? evlbm::ref_macro_f64(c->Q, c->K, c->scratch, c->RT_iso, c->f[c->cur], c->g[c->cur],
+                                                  c->stream)
+                            : evlbm::ref_macro_f32(c->P.precision, c->Q, c->K, c->scratch, c->RT_iso,
+                                                   c->f[c->cur], c->g[c->cur], c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moment stages");
+    return LBM_OK;
+}
+
+// Copies `count` scratch values starting at field offset `off` (in units of N) to host doubles.
+int copy_field(lbm_ctx *c, long long off, long long count, double *dst, double scale_div)
+{
+    const size_t bytes = c->real_bytes * (size_t)count;
+    const char *src = static_cast<const char *>(c->scratch) + c->real_bytes * (size_t)(off * c->N);
+    if (fp64(c)) {
+        CK(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (scale_div != 1.0)
+            for (long long k = 0; k < count; ++k) dst[k] = dst[k] / scale_div;
+    } else {
+        std::vector<float> tmp((size_t)count);
+        CK(c, cudaMemcpyAsync(tmp.data(), src, bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        for (long long k = 0; k < count; ++k) dst[k] = double(tmp[k]) / scale_div;
+    }
+    return LBM_OK;
+}
+
+void free_all(lbm_ctx *c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c->f[k]) cudaFree(c->f[k]);
+        if (c->g[k]) cudaFree(c->g[k]);
+    }
+    if (c->RT_iso) cudaFree(c->RT_iso);
+    if (c->scratch) cudaFree(c->scratch);
+    if (c->red) cudaFree(c->red);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_init(const lbm_params *params, const double *rho, const double *u, const double *T, void *stream,
+             lbm_ctx **out)
+{
+    g_init_err[0] = 0;
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(params);
+    if (rc) return rc;
+    if (!rho || !u || !T) return fail(nullptr, LBM_EINVAL, "rho, u and T must be host arrays");
+
+    lbm_ctx *c = static_cast<lbm_ctx *>(calloc(1, sizeof(lbm_ctx)));
+    if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    c->P = *params;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->Q = params->lattice == LBM_D2Q9 ? 9 : 27;
+    c->D = params->lattice == LBM_D2Q9 ? 2 : 3;
+    c->N = (long long)params->nx * params->ny * params->nz;
+    c->pop_bytes = params->precision == LBM_FP64 ? 8 : (params->precision == LBM_FP32 ? 4 : 2);
+    c->real_bytes = params->precision == LBM_FP64 ? 8 : 4;
+    const long long N = c->N;
+    const int D = c->D;
+
+    // Host-side checks of the initial fields and the deviation references.
+    double rsum = 0.0, esum = 0.0;
+    for (long long n = 0; n < N; ++n) {
+        if (!(rho[n] > 0.0) || !isfinite(rho[n]) || !(T[n] > 0.0) || !isfinite(T[n])) {
+            free(c);
+            return fail(nullptr, LBM_ENONFINITE, "rho and T must be finite and > 0 (node %lld)", n);
+        }
+        for (int a = 0; a < D; ++a)
+            if (!isfinite(u[a * N + n])) {
+                free(c);
+                return fail(nullptr, LBM_ENONFINITE, "u must be finite (node %lld)", n);
+            }
+        rsum += rho[n];
+        esum += 1.5 * params->R * T[n];
+    }
+    fill_kparams(c, rsum / double(N), esum / double(N));
+
+    // Device state.
+    const size_t pop = c->pop_bytes * (size_t)c->Q * (size_t)N;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&c->f[k], pop);
+        if (e == cudaSuccess && params->thermal) e = cudaMalloc(&c->g[k], pop);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c->red, evlbm::totals_work_bytes(N));
+    if (e == cudaSuccess) e = cudaMalloc(&c->RT_iso, c->real_bytes * (size_t)N);
+    void *d_fields = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d_fields, c->real_bytes * (size_t)(D + 2) * (size_t)N);
+    if (e != cudaSuccess) {
+        const int code = cuda_fail(nullptr, e, "lbm_init allocation");
+        if (d_fields) cudaFree(d_fields);
+        free_all(c);
+        free(c);
+        return code;
+    }
+
+    // Fields in the scratch precision: rho [N], u [D][N], RT [N] = R*T.
+    const size_t nf = (size_t)(D + 2) * (size_t)N;
+    if (c->real_bytes == 8) {
+        std::vector<double> h(nf);
+        memcpy(h.data(), rho, sizeof(double) * N);
+        memcpy(h.data() + N, u, sizeof(double) * D * N);
+        for (long long n = 0; n < N; ++n) h[(D + 1) * N + n] = params->R * T[n];
+        e = cudaMemcpyAsync(d_fields, h.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    } else {
+        std::vector<float> h(nf);
+        for (long long n = 0; n < N; ++n) h[n] = float(rho[n]);
+        for (long long k = 0; k < D * N; ++k) h[N + k] = float(u[k]);
+        for (long long n = 0; n < N; ++n) h[(D + 1) * N + n] = float(params->R * T[n]);
+        e = cudaMemcpyAsync(d_fields, h.data(), sizeof(float) * nf, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    const char *dF = static_cast<const char *>(d_fields);
+    const void *d_rho = dF, *d_u = dF + c->real_bytes * N, *d_RT = dF + c->real_bytes * (D + 1) * N;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->RT_iso, d_RT, c->real_bytes * N, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = fp64(c) ? evlbm::ref_init_f64(c->Q, c->K, d_rho, d_u, d_RT, c->f[0], c->g[0], c->stream)
+                    : evlbm::ref_init_f32(params->precision, c->Q, c->K, d_rho, d_u, d_RT, c->f[0], c->g[0],
+                                          c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_fields);
+    if (e != cudaSuccess) {
+        const int code = cuda_fail(nullptr, e, "lbm_init");
+        free_all(c);
+        free(c);
+        return code;
+    }
+    c->cur = 0;
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int n_steps)
+{
+    if (!c) return LBM_EINVAL;
+    if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps must be >= 0");
+    const bool fused = !fp64(c) && evlbm::fused2d_supported(c->P.precision, c->Q, c->K);
+    if (!fused) {
+        int rc = ensure_scratch(c);
+        if (rc) return rc;
+    }
+    for (int s = 0; s < n_steps; ++s) {
+        const int nx = c->cur ^ 1;
+        cudaError_t e;
+        if (fused)
+            e = evlbm::fused2d_step(c->P.precision, c->K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx], c->RT_iso,
+                                    c->stream);
+        else if (fp64(c))
+            e = evlbm::ref_step_f64(c->Q, c->K, c->scratch, c->RT_iso, c->f[c->cur], c->g[c->cur], c->f[nx],
+                                    c->g[nx], c->stream);
+        else
+            e = evlbm::ref_step_f32(c->P.precision, c->Q, c->K, c->scratch, c->RT_iso, c->f[c->cur], c->g[c->cur],
+                                    c->f[nx], c->g[nx], c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step");
+        c->cur = nx;
+        c->steps++;
+    }
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx *c, double *rho, double *u, double *T, double *F)
+{
+    if (!c) return LBM_EINVAL;
+    int rc = run_macro(c);
+    if (rc) return rc;
+    using O = evlbm::FieldOffsets;
+    const long long N = c->N;
+    if (rho && (rc = copy_field(c, O::rho, N, rho, 1.0))) return rc;
+    if (u && (rc = copy_field(c, O::u, c->D * N, u, 1.0))) return rc;
+    if (T && (rc = copy_field(c, O::RT, N, T, c->P.R))) return rc;
+    if (F && (rc = copy_field(c, O::F, c->D * N, F, 1.0))) return rc;
+    return LBM_OK;
+}
+
+int lbm_moments_device(lbm_ctx *c, float *d_rho, float *d_u, float *d_T)
+{
+    if (!c) return LBM_EINVAL;
+    int rc = run_macro(c);
+    if (rc) return rc;
+    cudaError_t e = fp64(c) ? evlbm::ref_export_f64(c->Q, c->K, c->scratch, c->P.R, d_rho, d_u, d_T, c->stream)
+                            : evlbm::ref_export_f32(c->Q, c->K, c->scratch, c->P.R, d_rho, d_u, d_T, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_moments_device");
+    return LBM_OK;
+}
+
+int lbm_populations(lbm_ctx *c, double *f, double *g)
+{
+    if (!c || !f) return c ? fail(c, LBM_EINVAL, "f is NULL") : LBM_EINVAL;
+    const size_t cnt = (size_t)c->Q * (size_t)c->N;
+    if (fp64(c)) {
+        CK(c, cudaMemcpyAsync(f, c->f[c->cur], sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+        if (g && c->P.thermal)
+            CK(c, cudaMemcpyAsync(g, c->g[c->cur], sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
+    double *tmp = nullptr;
+    CK(c, cudaMalloc(&tmp, sizeof(double) * cnt));
+    for (int which = 0; which < (c->P.thermal && g ? 2 : 1); ++which) {
+        cudaError_t e = evlbm::expand_f32(c->P.precision, c->Q, c->K, which ? c->g[c->cur] : c->f[c->cur], tmp, which,
+                                          c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(which ? g : f, tmp, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_fail(c, e, "lbm_populations");
+        }
+    }
+    cudaFree(tmp);
+    return LBM_OK;
+}
+
+int lbm_conserved(lbm_ctx *c, double out[5])
+{
+    if (!c || !out) return c ? fail(c, LBM_EINVAL, "out is NULL") : LBM_EINVAL;
+    int bad = 0;
+    cudaError_t e = evlbm::totals(c->P.precision, c->Q, c->K, c->f[c->cur], c->g[c->cur], c->red, out, &bad, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_conserved");
+    if (bad) return fail(c, LBM_ENONFINITE, "non-finite population after %lld steps", c->steps);
+    return LBM_OK;
+}
+
+long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
+
+int lbm_launches_per_step(const lbm_ctx *c)
+{
+    if (!c) return -1;
+    return (!fp64(c) && evlbm::fused2d_supported(c->P.precision, c->Q, c->K)) ? 1 : 4;
+}
+
+int lbm_sync(lbm_ctx *c)
+{
+    if (!c) return LBM_EINVAL;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_free(lbm_ctx *c)
+{
+    if (!c) return LBM_OK;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    free(c);
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err : g_init_err; }
+
+int lbm_critical_point(int eos, double a, double b, double out[2])
+{
+    if (!out || (eos != LBM_EOS_VDW && eos != LBM_EOS_CS) || !(a > 0.0) || !(b > 0.0)) return LBM_EINVAL;
+    if (eos == LBM_EOS_VDW) {
+        out[0] = 1.0 / (3.0 * b);
+        out[1] = 8.0 * a / (27.0 * b);
+        return LBM_OK;
+    }
+    auto y1 = [](double e) { return (1 + 4 * e + 4 * e * e - 4 * e * e * e + e * e * e * e) / pow(1 - e, 4); };
+    auto y2 = [](double e) {
+        return (4 + 8 * e - 12 * e * e + 4 * e * e * e) / pow(1 - e, 4) +
+               4 * (1 + 4 * e + 4 * e * e - 4 * e * e * e + e * e * e * e) / pow(1 - e, 5);
+    };
+    double lo = 0.01, hi = 0.4;
+    for (int k = 0; k < 200; ++k) {
+        const double mid = 0.5 * (lo + hi);
+        if ((y1(lo) - lo * y2(lo)) * (y1(mid) - mid * y2(mid)) <= 0) hi = mid;
+        else lo = mid;
+    }
+    const double eta = 0.5 * (lo + hi);
+    out[0] = 4.0 * eta / b;
+    out[1] = 8.0 * a / (b * y2(eta));
+    return LBM_OK;
+}
+
+int lbm_coexistence(int eos, double a, double b, double RT, double out[2])
+{
+    double crit[2];
+    if (!out || lbm_critical_point(eos, a, b, crit) != LBM_OK) return LBM_EINVAL;
+    if (!(RT > 0.0) || !(RT < crit[1])) return LBM_EINVAL;
+    int status = 0;
+    cudaError_t e = evlbm::coexistence(eos, a, b, RT, crit[0], out, &status);
+    if (e != cudaSuccess) return LBM_ECUDA;
+    if (status == 1) return LBM_EINVAL;
+    if (status != 0) return LBM_ETIMEOUT;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// Host-side entry points of the kernel translation units (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace evlbm {
+
+// Stage kernels in FP64 (reference order, no contraction): storage FP64.
+cudaError_t ref_init_f64(int Q, const KParams &p, const void *rho, const void *u, const void *RT, void *f, void *g,
+                         cudaStream_t st);
+cudaError_t ref_macro_f64(int Q, const KParams &p, void *scratch, const void *RT_iso, const void *f, const void *g,
+                          cudaStream_t st);
+cudaError_t ref_step_f64(int Q, const KParams &p, void *scratch, const void *RT_iso, const void *f, const void *g,
+                         void *fo, void *go, cudaStream_t st);
+cudaError_t ref_export_f64(int Q, const KParams &p, void *scratch, double R, float *rho, float *u, float *T,
+                           cudaStream_t st);
+cudaError_t expand_f64(int Q, const KParams &p, const void *src, double *dst, int which, cudaStream_t st);
+
+// Stage kernels in FP32; storage 1 = FP32, 2 = FP16 deviations, 3 = BF16 deviations.
+cudaError_t ref_init_f32(int prec, int Q, const KParams &p, const void *rho, const void *u, const void *RT, void *f,
+                         void *g, cudaStream_t st);
+cudaError_t ref_macro_f32(int prec, int Q, const KParams &p, void *scratch, const void *RT_iso, const void *f,
+                          const void *g, cudaStream_t st);
+cudaError_t ref_step_f32(int prec, int Q, const KParams &p, void *scratch, const void *RT_iso, const void *f,
+                         const void *g, void *fo, void *go, cudaStream_t st);
+cudaError_t ref_export_f32(int Q, const KParams &p, void *scratch, double R, float *rho, float *u, float *T,
+                           cudaStream_t st);
+cudaError_t expand_f32(int prec, int Q, const KParams &p, const void *src, double *dst, int which, cudaStream_t st);
+
+// Scratch layout of the stage kernels: rho, j, Gam, Pi, lap, A, F, u, RT, theta0, P0, gamma0, flux, wq.
+constexpr int kRefFieldCount = 30;
+struct FieldOffsets {
+    static constexpr long long rho = 0, j = 1, Gam = 4, Pi = 5, lap = 14, A = 15, F = 16, u = 19, RT = 22,
+                               theta0 = 23, P0 = 24, gamma0 = 25, flux = 26, wq = 29;
+};
+
+// Fused single-pass D2Q9 step (FP32 arithmetic); prec 1/2/3 as above.
+bool fused2d_supported(int prec, int Q, const KParams &p);
+cudaError_t fused2d_step(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
+                         const void *RT_iso, cudaStream_t st);
+
+// FP64 totals of the state (mass, momentum x/y/z, energy) and a non-finite flag.
+// `work` must hold at least totals_work_bytes(N) bytes.
+size_t totals_work_bytes(long long N);
+cudaError_t totals(int prec, int Q, const KParams &p, const void *f, const void *g, void *work, double *h_out,
+                   int *h_nonfinite, cudaStream_t st);
+
+// Maxwell construction in FP64 on the GPU.
+cudaError_t coexistence(int eos, double a, double b, double RT, double rho_c, double *h_out, int *h_status);
+
+}  // namespace evlbm

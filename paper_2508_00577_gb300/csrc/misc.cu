@@ -1,0 +1,222 @@
+// FP64 device reductions of the conserved totals and the FP64 Maxwell
+// construction of the coexisting densities.
+#include <math.h>
+#include "dispatch.h"
+
+namespace evlbm {
+
+namespace {
+
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs
+constexpr int kRedThreads = 256;
+
+template <typename S>
+__device__ __forceinline__ double pop64(const S *p, float off)
+{
+    if constexpr (Store<S>::dev)
+        return double(off) + double(Store<S>::load(p));
+    else
+        return double(Store<S>::load(p));
+}
+
+// Each thread sums its nodes in ascending order, the block combines the threads
+// in a fixed tree; the result does not depend on scheduling.
+template <typename S, int Q>
+__global__ void __launch_bounds__(kRedThreads) k_totals_partial(KParams p, const S *f, const S *g, double *partial,
+                                                                 int *nonfinite)
+{
+    __shared__ double sh[5][kRedThreads];
+    double acc[5] = {0, 0, 0, 0, 0};
+    int bad = 0;
+    const long long N = p.N;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double fi = pop64<S>(f + i * N + n, p.foff[i]);
+            bad |= !isfinite(fi);
+            acc[0] += fi;
+            const int c[3] = {cx_of(i), cy_of(i), cz_of(i, Q)};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                acc[1 + a] += c[a] == 1 ? fi : (c[a] == -1 ? -fi : 0.0);
+            if (p.thermal) {
+                const double gi = pop64<S>(g + i * N + n, p.goff[i]);
+                bad |= !isfinite(gi);
+                acc[4] += gi;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) partial[k * kRedBlocks + blockIdx.x] = sh[k][0];
+    if (bad) atomicOr(nonfinite, 1);
+}
+
+__global__ void k_totals_final(const double *partial, double *out)
+{
+    __shared__ double sh[5][1024];
+    for (int k = 0; k < 5; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) v += partial[k * kRedBlocks + b];
+        sh[k][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; ++k) out[k] = sh[k][0];
+}
+
+template <typename S>
+cudaError_t totals_s(int Q, const KParams &p, const void *f, const void *g, void *work, cudaStream_t st)
+{
+    double *partial = static_cast<double *>(work);
+    double *out = partial + 5 * kRedBlocks;
+    int *flag = reinterpret_cast<int *>(out + 8);
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if (Q == 9)
+        k_totals_partial<S, 9><<<kRedBlocks, kRedThreads, 0, st>>>(p, static_cast<const S *>(f),
+                                                                  static_cast<const S *>(g), partial, flag);
+    else
+        k_totals_partial<S, 27><<<kRedBlocks, kRedThreads, 0, st>>>(p, static_cast<const S *>(f),
+                                                                   static_cast<const S *>(g), partial, flag);
+    k_totals_final<<<1, 1024, 0, st>>>(partial, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Maxwell construction: p(rho_v) = p(rho_l), mu(rho_v) = mu(rho_l) for
+// p = P_E - a rho^2 (Enskog pressure in the vdW or Carnahan-Starling form plus
+// the Vlasov pressure), by bisection on the pressure level and Newton polish.
+// ---------------------------------------------------------------------------
+struct Eos {
+    int kind;
+    double a, b, RT;
+    __device__ double rho_max() const { return kind == 0 ? 1.0 / b : 4.0 / b; }
+    __device__ double p(double r) const
+    {
+        if (kind == 0) return r * RT / (1.0 - b * r) - a * r * r;
+        const double e = 0.25 * b * r;
+        return r * RT * (1.0 + e + e * e - e * e * e) / ((1.0 - e) * (1.0 - e) * (1.0 - e)) - a * r * r;
+    }
+    __device__ double dp(double r) const
+    {
+        if (kind == 0) return RT / ((1.0 - b * r) * (1.0 - b * r)) - 2.0 * a * r;
+        const double e = 0.25 * b * r, om = 1.0 - e;
+        return RT * (1.0 + 4.0 * e + 4.0 * e * e - 4.0 * e * e * e + e * e * e * e) / (om * om * om * om) -
+               2.0 * a * r;
+    }
+    __device__ double mu(double r) const
+    {
+        if (kind == 0) return RT * (log(r / (1.0 - b * r)) + b * r / (1.0 - b * r)) - 2.0 * a * r;
+        const double e = 0.25 * b * r, om = 1.0 - e;
+        return RT * (log(r) + (8.0 * e - 9.0 * e * e + 3.0 * e * e * e) / (om * om * om)) - 2.0 * a * r;
+    }
+};
+
+// Root of a monotone function on [lo, hi] by bisection (fixed number of halvings).
+template <typename Fn>
+__device__ double bisect(Fn fn, double lo, double hi)
+{
+    double flo = fn(lo);
+    for (int k = 0; k < 200; ++k) {
+        const double mid = 0.5 * (lo + hi), fm = fn(mid);
+        if ((flo <= 0.0) == (fm <= 0.0)) {
+            lo = mid;
+            flo = fm;
+        } else {
+            hi = mid;
+        }
+    }
+    return 0.5 * (lo + hi);
+}
+
+__global__ void k_coexistence(Eos E, double rho_c, double *out, int *status)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double rmax = E.rho_max() * (1.0 - 1e-12);
+    // Spinodal densities: dp/drho = 0 on either side of the critical density.
+    const double s1 = bisect([&](double r) { return E.dp(r); }, 1e-12 * rho_c, rho_c);
+    const double s2 = bisect([&](double r) { return E.dp(r); }, rho_c, rmax);
+    if (!(E.dp(0.5 * (s1 + s2)) < 0.0)) {
+        *status = 1;   // no van der Waals loop: above the critical temperature
+        return;
+    }
+    double Plo = fmax(E.p(s2), 0.0), Phi = E.p(s1), rv = 0.0, rl = 0.0;
+    for (int k = 0; k < 200; ++k) {
+        const double P = 0.5 * (Plo + Phi);
+        rv = bisect([&](double r) { return E.p(r) - P; }, 1e-300, s1);
+        rl = bisect([&](double r) { return E.p(r) - P; }, s2, rmax);
+        if (E.mu(rl) < E.mu(rv)) Phi = P;   // liquid favoured: above saturation
+        else Plo = P;
+    }
+    int it = 0;
+    for (; it < 100; ++it) {
+        const double F1 = E.p(rl) - E.p(rv), F2 = E.mu(rl) - E.mu(rv);
+        const double pl = E.dp(rl), pv = E.dp(rv);
+        // Jacobian of (F1, F2) in (rv, rl): dmu/drho = (dp/drho)/rho.
+        const double J11 = -pv, J12 = pl, J21 = -pv / rv, J22 = pl / rl;
+        const double det = J11 * J22 - J12 * J21;
+        const double dv = (-F1 * J22 + F2 * J12) / det;
+        const double dl = (-F2 * J11 + F1 * J21) / det;
+        rv += dv;
+        rl += dl;
+        if (fabs(dv) <= 1e-13 * rv && fabs(dl) <= 1e-13 * rl) break;
+    }
+    out[0] = rv;
+    out[1] = rl;
+    *status = (it < 100 && rv > 0.0 && rl > rv) ? 0 : 2;
+}
+
+}  // namespace
+
+size_t totals_work_bytes(long long) { return sizeof(double) * (5 * kRedBlocks + 8) + 64; }
+
+cudaError_t totals(int prec, int Q, const KParams &p, const void *f, const void *g, void *work, double *h_out,
+                   int *h_nonfinite, cudaStream_t st)
+{
+    cudaError_t e;
+    switch (prec) {
+    case 0: e = totals_s<double>(Q, p, f, g, work, st); break;
+    case 1: e = totals_s<float>(Q, p, f, g, work, st); break;
+    case 2: e = totals_s<__half>(Q, p, f, g, work, st); break;
+    default: e = totals_s<__nv_bfloat16>(Q, p, f, g, work, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    double *out = static_cast<double *>(work) + 5 * kRedBlocks;
+    if ((e = cudaMemcpyAsync(h_out, out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(h_nonfinite, out + 8, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t coexistence(int eos, double a, double b, double RT, double rho_c, double *h_out, int *h_status)
+{
+    void *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 4 * sizeof(double));
+    if (e != cudaSuccess) return e;
+    double *d_out = static_cast<double *>(buf);
+    int *d_status = reinterpret_cast<int *>(d_out + 2);
+    Eos E{eos, a, b, RT};
+    k_coexistence<<<1, 32>>>(E, rho_c, d_out, d_status);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(h_out, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    return e;
+}
+
+}  // namespace evlbm

@@ -1,0 +1,82 @@
+"""The C ABI library builds, loads and exports every symbol include/evlbm.h declares;
+argument validation happens on the host before any GPU work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle.eos as E
+import paper_2508_00577_gb300 as ev
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "evlbm.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:int|long long|const char \*)\s*(lbm_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_binding_names():
+    assert declared_symbols() == sorted(ev.EXPORTED_SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = ev.lib()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
+def test_params_struct_matches_header():
+    """Field order and types of lbm_params as in the header."""
+    text = open(HEADER).read()
+    body = text[text.index("typedef struct {"):text.index("} lbm_params;")]
+    names = re.findall(r"^\s*(?:int|double)\s+([\w, ]+);", body, re.M)
+    flat = [n.strip() for group in names for n in group.split(",")]
+    assert [f[0].rstrip("_") for f in ev.lbm_params._fields_] == flat
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("lattice", 5), ("tau", 0.0), ("lambda_", -1.0),
+                                         ("precision", 7), ("R", 0.0), ("thermal", 3), ("eos", 9)])
+def test_invalid_params_rejected_on_host(field, value):
+    p = ev.lbm_params.make(nx=4, ny=4)
+    setattr(p, field, value)
+    N = 16
+    with pytest.raises(ev.LBMError) as e:
+        ev.lbm_init(p, np.ones(N), np.zeros((2, N)), np.ones(N))
+    assert e.value.code == ev.LBM_EINVAL
+    assert ev.lbm_last_error(None)
+
+
+def test_nonpositive_fields_rejected_on_host():
+    p = ev.lbm_params.make(nx=4, ny=4)
+    rho = np.ones(16)
+    rho[5] = -1.0
+    with pytest.raises(ev.LBMError) as e:
+        ev.lbm_init(p, rho, np.zeros((2, 16)), np.ones(16))
+    assert e.value.code == ev.LBM_ENONFINITE
+    assert "node 5" in ev.lbm_last_error(None)
+
+
+def test_null_context_is_invalid():
+    L = ev.lib()
+    assert L.lbm_step(None, 1) == ev.LBM_EINVAL
+    assert L.lbm_free(None) == ev.LBM_OK
+    assert L.lbm_step_count(None) == -1
+
+
+@pytest.mark.parametrize("eos,a,b", [(ev.LBM_EOS_CS, 0.1, 4.0), (ev.LBM_EOS_VDW, 9 / 392, 2 / 21)])
+def test_critical_point_host(eos, a, b):
+    rc, Tc = ev.lbm_critical_point(eos, a, b)
+    orc, oTc = E.critical_point(eos, a, b)
+    assert rc == pytest.approx(orc, rel=1e-10)
+    assert Tc == pytest.approx(oTc, rel=1e-10)
+
+
+def test_coexistence_rejects_supercritical_on_host():
+    _, Tc = ev.lbm_critical_point(ev.LBM_EOS_CS, 0.1, 4.0)
+    with pytest.raises(ev.LBMError) as e:
+        ev.lbm_coexistence(ev.LBM_EOS_CS, 0.1, 4.0, 1.01 * Tc)
+    assert e.value.code == ev.LBM_EINVAL

@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 CPU oracle.
+
+FP64: populations bit-identical to the oracle (same operation order, no FMA
+contraction on either side).  FP32: max |d rho|/rho <= 1e-5.  FP16/BF16
+deviation storage: max |d rho|/rho <= 1e-3.  Inputs come from the seeded
+generators in paper_2508_00577_gb300.inputs; coexisting densities and kappa
+from the oracle's EOS module.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.eos as E
+import paper_2508_00577_gb300 as ev
+from paper_2508_00577_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+A, B = 0.1, 4.0
+TOL = {ev.LBM_FP32: 1e-5, ev.LBM_FP16_DEV: 1e-3, ev.LBM_BF16_DEV: 1e-3}
+
+
+def thermo(tr, eos=E.CS, a=A, b=B, width=4.0):
+    _, Tc = E.critical_point(eos, a, b)
+    RT = tr * Tc
+    rv, rl = E.maxwell(eos, a, b, RT)
+    return RT, rv, rl, E.kappa_for_width(eos, a, b, RT, width)
+
+
+def pair(Q, nx, ny, nz, fields, kappa, precision, eos=E.CS, a=A, b=B, thermal=1, force_form=0, tau=0.3):
+    """(oracle state, GPU lattice) from the same fields and parameters."""
+    op = oracle.Params(Q=Q, nx=nx, ny=ny, nz=nz, eos=eos, a=a, b=b, kappa=kappa, tau=tau, thermal=thermal,
+                       force_form=force_form)
+    gp = ev.lbm_params.make(lattice=ev.LBM_D2Q9 if Q == 9 else ev.LBM_D3Q27, nx=nx, ny=ny, nz=nz, eos=eos, a=a,
+                            b=b, kappa=kappa, tau=tau, thermal=thermal, precision=precision,
+                            force_form=force_form)
+    rho, u, T = fields
+    return oracle.State(op, rho, u, T), ev.Lattice(gp, rho, u, T)
+
+
+def droplet_fields(nx, ny, nz, tr=0.8, R=None):
+    RT, rv, rl, kappa = thermo(tr)
+    R = R if R is not None else 0.3 * min(nx, ny)
+    rho, u, T = inputs.droplet(nx, ny, R, rv, rl, RT)
+    return (np.tile(rho, nz), np.tile(u, (1, nz)), np.tile(T, nz)), kappa
+
+
+def assert_bitexact(o, g):
+    f, gg = g.populations()
+    assert np.array_equal(f, o.f), f"max |df| = {np.abs(f - o.f).max()}"
+    if gg is not None:
+        assert np.array_equal(gg, o.g), f"max |dg| = {np.abs(gg - o.g).max()}"
+
+
+# ---------------------------------------------------------------------------
+# FP64: bit-exact
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nx,ny,nz", [(48, 40, 1), (37, 23, 1), (1, 1, 1), (5, 1, 2), (33, 17, 3)])
+def test_fp64_bitexact_d2q9_droplet(nx, ny, nz):
+    fields, kappa = droplet_fields(nx, ny, nz)
+    o, g = pair(9, nx, ny, nz, fields, kappa, ev.LBM_FP64)
+    assert_bitexact(o, g)                     # initial equilibria
+    for n in (1, 9, 40):
+        o.step(n)
+        g.step(n)
+        assert_bitexact(o, g)
+
+
+def test_fp64_bitexact_slab_2000_steps():
+    """64 x 64 D2Q9 planar slab (width 32, tanh width 4) at T/Tc = 0.8, 2000 steps."""
+    RT, rv, rl, kappa = thermo(0.8)
+    fields = inputs.slab(64, 64, rv, rl, RT, thickness=32.0, width=4.0)
+    o, g = pair(9, 64, 64, 1, fields, kappa, ev.LBM_FP64)
+    o.step(2000)
+    g.step(2000)
+    assert_bitexact(o, g)
+    # mass conserved to rounding on the GPU too
+    assert g.conserved()[0] == pytest.approx(o.totals()[0], rel=1e-13)
+
+
+@pytest.mark.parametrize("variant", ["isothermal", "literal", "vdw"])
+def test_fp64_bitexact_variants(variant):
+    nx, ny = 40, 36
+    if variant == "vdw":
+        a, b = 9 / 392 * 0.1, 2 / 21
+        RT, rv, rl, kappa = thermo(0.9, E.VDW, a, b)
+        fields = inputs.droplet(nx, ny, 11.0, rv, rl, RT)
+        o, g = pair(9, nx, ny, 1, fields, kappa, ev.LBM_FP64, eos=E.VDW, a=a, b=b)
+    else:
+        fields, kappa = droplet_fields(nx, ny, 1, tr=0.9)
+        o, g = pair(9, nx, ny, 1, fields, kappa, ev.LBM_FP64, thermal=0 if variant == "isothermal" else 1,
+                    force_form=1 if variant == "literal" else 0)
+    o.step(60)
+    g.step(60)
+    assert_bitexact(o, g)
+
+
+@pytest.mark.parametrize("thermal", [1, 0])
+def test_fp64_bitexact_d3q27(thermal):
+    """16^3 (and a ragged 11 x 7 x 5) D3Q27 spinodal noise at T/Tc = 0.85."""
+    for nx, ny, nz in ((16, 16, 16), (11, 7, 5)):
+        RT, rv, rl, kappa = thermo(0.85)
+        s1, s2 = E.spinodal(E.CS, A, B, RT)
+        fields = inputs.spinodal_noise(nx, ny, nz, 0.5 * (s1 + s2), RT, amplitude=0.01)
+        o, g = pair(27, nx, ny, nz, fields, kappa, ev.LBM_FP64, thermal=thermal)
+        o.step(12)
+        g.step(12)
+        assert_bitexact(o, g)
+
+
+def test_fp64_moments_bitexact():
+    fields, kappa = droplet_fields(30, 26, 1)
+    o, g = pair(9, 30, 26, 1, fields, kappa, ev.LBM_FP64)
+    o.step(25)
+    g.step(25)
+    want = o.macro()
+    got = g.moments()
+    for w, h in zip(want, got):
+        assert np.array_equal(w, h)
+
+
+# ---------------------------------------------------------------------------
+# FP32 and reduced-precision storage: tolerances on rho
+# ---------------------------------------------------------------------------
+
+def rel_rho_err(o, g):
+    ro = o.macro()[0]
+    rg = g.moments()[0]
+    return np.max(np.abs(rg - ro) / ro)
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(96, 80, 1), (130, 70, 2), (257, 33, 1), (7, 5, 1), (1, 1, 1), (300, 260, 1)])
+def test_fp32_d2q9(nx, ny, nz):
+    """FP32 (fused single-pass kernel for D2Q9): max |d rho|/rho <= 1e-5 after 100 steps.
+    Sizes span several strips/row chunks, ragged tails and degenerate 1-node lattices."""
+    fields, kappa = droplet_fields(nx, ny, nz)
+    o, g = pair(9, nx, ny, nz, fields, kappa, ev.LBM_FP32)
+    assert rel_rho_err(o, g) <= 1e-6
+    o.step(1)
+    g.step(1)
+    assert rel_rho_err(o, g) <= 1e-6
+    o.step(99)
+    g.step(99)
+    assert rel_rho_err(o, g) <= 1e-5
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 48), (300, 40)])
+def test_fp32_d2q9_isothermal(nx, ny):
+    fields, kappa = droplet_fields(nx, ny, 1, tr=0.9)
+    o, g = pair(9, nx, ny, 1, fields, kappa, ev.LBM_FP32, thermal=0)
+    o.step(100)
+    g.step(100)
+    assert rel_rho_err(o, g) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", [ev.LBM_FP16_DEV, ev.LBM_BF16_DEV])
+@pytest.mark.parametrize("nx,ny,nz", [(96, 80, 1), (130, 70, 2)])
+def test_reduced_precision_d2q9(precision, nx, ny, nz):
+    fields, kappa = droplet_fields(nx, ny, nz)
+    o, g = pair(9, nx, ny, nz, fields, kappa, precision)
+    o.step(100)
+    g.step(100)
+    err = rel_rho_err(o, g)
+    assert err <= TOL[precision], err
+
+
+def test_fp32_long_run_droplet():
+    """FP32 storage rounds every population once per step, so the FP32 - FP64 density
+    difference drifts by about one FP32 ulp per step; over 2000 steps (128^2, R = 32)
+    it stays below 2e-4."""
+    fields, kappa = droplet_fields(128, 128, 1, R=32.0)
+    o, g = pair(9, 128, 128, 1, fields, kappa, ev.LBM_FP32)
+    o.step(2000)
+    g.step(2000)
+    assert rel_rho_err(o, g) <= 2e-4
+
+
+# ---------------------------------------------------------------------------
+# Other entry points
+# ---------------------------------------------------------------------------
+
+def test_moments_device_matches_host():
+    torch = pytest.importorskip("torch")
+    fields, kappa = droplet_fields(64, 48, 1)
+    gp = ev.lbm_params.make(nx=64, ny=48, kappa=kappa, precision=ev.LBM_FP32)
+    with ev.Lattice(gp, *fields) as g:
+        g.step(10)
+        rho_h, u_h, T_h, _ = g.moments()
+        rho = torch.empty(gp.N, device="cuda", dtype=torch.float32)
+        u = torch.empty(2 * gp.N, device="cuda", dtype=torch.float32)
+        T = torch.empty(gp.N, device="cuda", dtype=torch.float32)
+        ev.lbm_moments_device(g.ctx, rho.data_ptr(), u.data_ptr(), T.data_ptr())
+        ev.lbm_sync(g.ctx)
+        np.testing.assert_allclose(rho.cpu().numpy(), rho_h, rtol=1e-7)
+        np.testing.assert_allclose(T.cpu().numpy(), T_h, rtol=1e-6)
+        np.testing.assert_allclose(u.cpu().numpy(), u_h.ravel(), atol=1e-9)
+
+
+@pytest.mark.parametrize("eos,a,b", [(E.CS, A, B), (E.VDW, 9 / 392, 2 / 21)])
+@pytest.mark.parametrize("tr", [0.7, 0.85, 0.95])
+def test_coexistence_fp64_on_gpu(eos, a, b, tr):
+    _, Tc = E.critical_point(eos, a, b)
+    rv, rl = ev.lbm_coexistence(eos, a, b, tr * Tc)
+    ov, ol = E.maxwell(eos, a, b, tr * Tc)
+    assert rv == pytest.approx(ov, rel=1e-10)
+    assert rl == pytest.approx(ol, rel=1e-10)
+
+
+def test_step_count_and_zero_steps():
+    fields, kappa = droplet_fields(16, 16, 1)
+    gp = ev.lbm_params.make(nx=16, ny=16, kappa=kappa, precision=ev.LBM_FP64)
+    with ev.Lattice(gp, *fields) as g:
+        f0, _ = g.populations()
+        g.step(0)
+        assert ev.lbm_step_count(g.ctx) == 0
+        assert np.array_equal(g.populations()[0], f0)
+        g.step(3)
+        assert ev.lbm_step_count(g.ctx) == 3
+
+
+def test_conserved_flags_nonfinite():
+    """An unstable state (here: a supercritical liquid far beyond the lattice's
+    stable sound speed) ends in non-finite populations; lbm_conserved reports it."""
+    _, Tc = E.critical_point(E.CS, 1.0, 4.0)
+    RT = 0.8 * Tc
+    fields = inputs.spinodal_noise(16, 16, 1, 0.3, RT, amplitude=0.01, D=2)
+    gp = ev.lbm_params.make(nx=16, ny=16, a=1.0, b=4.0, kappa=0.0, precision=ev.LBM_FP32)
+    with ev.Lattice(gp, *fields) as g:
+        g.step(2000)
+        with pytest.raises(ev.LBMError) as e:
+            g.conserved()
+        assert e.value.code == ev.LBM_ENONFINITE
