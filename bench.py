@@ -194,6 +194,11 @@ def run(args):
     N = params.N
     lat = ev.Lattice(params, rho, u, T, stream=stream.cuda_stream)
     launches_per_step = ev.lbm_launches_per_step(lat.ctx)
+    if args.tile:
+        ev.lbm_set_tile(lat.ctx, *(int(v) for v in args.tile.split(",")))
+        tile = ev.lbm_get_tile(lat.ctx)
+    else:
+        tile = ev.lbm_autotune(lat.ctx, 3) if not args.no_autotune else ev.lbm_get_tile(lat.ctx)
 
     # Warm-up
     lat.step(args.warmup)
@@ -234,6 +239,7 @@ def run(args):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     with ev.Lattice(params, pinned[0], pinned[1], pinned[2], stream=stream.cuda_stream) as lat2:
+        ev.lbm_set_tile(lat2.ctx, *tile)
         lat2.step(e2e_steps)
         ev.lbm_moments(lat2.ctx, out_rho, None, None, None)
     torch.cuda.synchronize(dev)
@@ -253,6 +259,7 @@ def run(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if nz == 9 else f"{nz} of the 9 layers of: {WORKLOAD}", "nodes_per_gpu": N, "layers": nz, "lattice": "D2Q9",
                    "thermal": True, "precision": "fp32", "l2": "inputs larger than L2 (1.36 GB/step)",
+                   "tile": {"w": tile[0], "h": tile[1], "autotuned": not (args.no_autotune or args.tile)},
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
@@ -276,6 +283,8 @@ def main():
     ap.add_argument("--layers", type=int, default=9, help="layers of the sweep (9 = the full workload)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile", default="", help="fixed launch shape W,H of the fused kernel")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -127,6 +127,24 @@ long long lbm_step_count(const lbm_ctx *ctx);
  * -1 for NULL. */
 int lbm_launches_per_step(const lbm_ctx *ctx);
 
+/* Launch shape of the fused single-pass kernel (used for D2Q9 at FP32): strips of
+ * tile_w columns (one of 64, 96, 128, 192) marching over chunks of tile_h rows
+ * (>= 1; rounded up to an even number, the kernel advances two rows at a time).
+ * tile_w = tile_h = 0 restores the size-based default.  Contexts without a fused
+ * kernel accept and ignore the shape.  Errors: LBM_EINVAL. */
+int lbm_set_tile(lbm_ctx *ctx, int tile_w, int tile_h);
+
+/* Current launch shape (0, 0 when the default is in use or no fused kernel applies). */
+int lbm_get_tile(const lbm_ctx *ctx, int *tile_w, int *tile_h);
+
+/* Autotuner: times every candidate launch shape of the fused kernel for
+ * probe_steps (>= 1) steps each with CUDA events on the context's stream and
+ * keeps the fastest.  The probes read the current state and write the spare
+ * buffer, so the state is unchanged.  Synchronises the stream.  The chosen shape
+ * is returned in *tile_w, *tile_h (either may be NULL); both are 0 when the
+ * context has no fused kernel.  Errors: LBM_EINVAL, LBM_ECUDA. */
+int lbm_autotune(lbm_ctx *ctx, int probe_steps, int *tile_w, int *tile_h);
+
 /* Wait for all work queued on the context's stream. */
 int lbm_sync(lbm_ctx *ctx);
 

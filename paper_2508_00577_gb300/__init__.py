@@ -16,7 +16,8 @@ import numpy as np
 
 __all__ = [
     "lbm_params", "lib", "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_device",
-    "lbm_populations", "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_sync", "lbm_free",
+    "lbm_populations", "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_set_tile",
+    "lbm_get_tile", "lbm_autotune", "lbm_sync", "lbm_free",
     "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "LBMError", "Lattice",
     "LBM_D2Q9", "LBM_D3Q27", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
     "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS",
@@ -33,8 +34,8 @@ _ERRNAMES = {LBM_EINVAL: "LBM_EINVAL", LBM_ECUDA: "LBM_ECUDA", LBM_ENOMEM: "LBM_
 # Every symbol include/evlbm.h declares.
 EXPORTED_SYMBOLS = (
     "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_populations",
-    "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_sync", "lbm_free",
-    "lbm_last_error", "lbm_coexistence", "lbm_critical_point",
+    "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_set_tile", "lbm_get_tile",
+    "lbm_autotune", "lbm_sync", "lbm_free", "lbm_last_error", "lbm_coexistence", "lbm_critical_point",
 )
 
 
@@ -96,6 +97,10 @@ def lib():
             L.lbm_step_count.argtypes = [vp]
             L.lbm_step_count.restype = ctypes.c_longlong
             L.lbm_launches_per_step.argtypes = [vp]
+            ip = ctypes.POINTER(ctypes.c_int)
+            L.lbm_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            L.lbm_get_tile.argtypes = [vp, ip, ip]
+            L.lbm_autotune.argtypes = [vp, ctypes.c_int, ip, ip]
             L.lbm_sync.argtypes = [vp]
             L.lbm_free.argtypes = [vp]
             L.lbm_last_error.argtypes = [vp]
@@ -182,6 +187,22 @@ def lbm_step_count(ctx):
 
 def lbm_launches_per_step(ctx):
     return lib().lbm_launches_per_step(ctx)
+
+
+def lbm_set_tile(ctx, tile_w, tile_h):
+    _check(lib().lbm_set_tile(ctx, int(tile_w), int(tile_h)), ctx)
+
+
+def lbm_get_tile(ctx):
+    w, h = ctypes.c_int(), ctypes.c_int()
+    _check(lib().lbm_get_tile(ctx, ctypes.byref(w), ctypes.byref(h)), ctx)
+    return w.value, h.value
+
+
+def lbm_autotune(ctx, probe_steps=3):
+    w, h = ctypes.c_int(), ctypes.c_int()
+    _check(lib().lbm_autotune(ctx, int(probe_steps), ctypes.byref(w), ctypes.byref(h)), ctx)
+    return w.value, h.value
 
 
 def lbm_sync(ctx):

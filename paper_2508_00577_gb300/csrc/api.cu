@@ -350,6 +350,76 @@ int lbm_launches_per_step(const lbm_ctx *c)
     return (!fp64(c) && evlbm::fused2d_supported(c->P.precision, c->Q, c->K)) ? 1 : 4;
 }
 
+int lbm_set_tile(lbm_ctx *c, int tile_w, int tile_h)
+{
+    if (!c) return LBM_EINVAL;
+    bool ok = tile_w == 0 && tile_h == 0;
+    for (int k = 0; k < evlbm::kFusedWidthCount; ++k) ok = ok || (tile_w == evlbm::kFusedWidths[k] && tile_h >= 1);
+    if (!ok) return fail(c, LBM_EINVAL, "tile_w must be one of 64,96,128,192 and tile_h >= 1 (or both 0)");
+    c->K.tile_w = tile_w;
+    c->K.tile_h = tile_h;
+    return LBM_OK;
+}
+
+int lbm_get_tile(const lbm_ctx *c, int *tile_w, int *tile_h)
+{
+    if (!c) return LBM_EINVAL;
+    if (tile_w) *tile_w = c->K.tile_w;
+    if (tile_h) *tile_h = c->K.tile_h;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
+{
+    if (!c || probe_steps < 1) return c ? fail(c, LBM_EINVAL, "probe_steps must be >= 1") : LBM_EINVAL;
+    if (tile_w) *tile_w = 0;
+    if (tile_h) *tile_h = 0;
+    if (fp64(c) || !evlbm::fused2d_supported(c->P.precision, c->Q, c->K)) return LBM_OK;
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    const int heights[] = {16, 32, 64, 128, 256};
+    const int nx = c->cur ^ 1;
+    float best = 1e30f;
+    int bw = 0, bh = 0;
+    KParams K = c->K;
+    cudaError_t e = cudaSuccess;
+    for (int wi = 0; wi < evlbm::kFusedWidthCount && e == cudaSuccess; ++wi) {
+        const int W = evlbm::kFusedWidths[wi];
+        if (W > 2 * c->P.nx && W != evlbm::kFusedWidths[0]) continue;
+        for (int hi = 0; hi < 5 && e == cudaSuccess; ++hi) {
+            const int H = heights[hi] < c->P.ny ? heights[hi] : c->P.ny;
+            if (hi > 0 && H == (heights[hi - 1] < c->P.ny ? heights[hi - 1] : c->P.ny)) continue;
+            K.tile_w = W;
+            K.tile_h = H;
+            // One untimed launch, then probe_steps timed ones; input stays c->f[c->cur].
+            for (int s = 0; s <= probe_steps && e == cudaSuccess; ++s) {
+                if (s == 1) e = cudaEventRecord(e0, c->stream);
+                if (e == cudaSuccess)
+                    e = evlbm::fused2d_step(c->P.precision, K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx],
+                                            c->RT_iso, c->stream);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                bw = W;
+                bh = H;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_autotune");
+    c->K.tile_w = bw;
+    c->K.tile_h = bh;
+    if (tile_w) *tile_w = bw;
+    if (tile_h) *tile_h = bh;
+    return LBM_OK;
+}
+
 int lbm_sync(lbm_ctx *c)
 {
     if (!c) return LBM_EINVAL;

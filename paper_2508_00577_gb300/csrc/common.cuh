@@ -21,6 +21,7 @@ struct KParams {
     double c_star;       // (dt/lambda)(1 - beta)
     double rho_ref;      // reference density of deviation storage
     double E_ref;        // reference energy of deviation storage
+    int tile_w, tile_h;  // launch shape of the fused kernel (0 = default)
     float foff[27];      // deviation offsets w_i rho_ref (0 for FP32/FP64 storage)
     float goff[27];      // deviation offsets w_i rho_ref E_ref
 };

@@ -35,7 +35,12 @@ struct FieldOffsets {
                                theta0 = 23, P0 = 24, gamma0 = 25, flux = 26, wq = 29;
 };
 
-// Fused single-pass D2Q9 step (FP32 arithmetic); prec 1/2/3 as above.
+// Fused single-pass D2Q9 step (FP32 arithmetic); prec 1/2/3 as above.  The
+// launch shape is a strip of tile_w columns marching over chunks of tile_h rows
+// (KParams::tile_w/tile_h; 0 = default).
+constexpr int kFusedWidthCount = 4;
+extern const int kFusedWidths[kFusedWidthCount];
+void fused2d_default_tile(const KParams &p, int *W, int *H);
 bool fused2d_supported(int prec, int Q, const KParams &p);
 cudaError_t fused2d_step(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
                          const void *RT_iso, cudaStream_t st);

@@ -9,38 +9,69 @@
 // (Eqs. feq, f_star, geq, gstar, g_corr) and the collision.
 //
 // Work decomposition.  A CTA owns a strip of W output columns of one 2-D layer
-// and marches down a chunk of H rows.  The force needs rho within radius 2 of
-// every node whose velocity is needed, and the corrections need u, T within
-// radius 1 of the collided node, so the pipeline runs four row stages that lag
-// each other by one row.  For the leading row L:
-//   A: rho(L), j(L)          pulled populations of row L        (W + 6 columns)
-//   B: Pi(L-1)               Korteweg stress from rho(L-2..L)   (W + 4 columns)
-//   C: F, u, T, EOS (L-2)    div Pi(L-3..L-1), Gamma(L-2)       (W + 2 columns)
-//   D: collide (L-3)         Phi, q' from fields(L-4..L-2)      (W columns)
-// Rows of each stage live in 4-deep ring buffers in shared memory; a thread owns
-// one column through all stages and keeps that column's centre values of the
-// next collision row in registers.  The 6 halo columns of a strip are owned by
-// an extra warp that takes part in stages A-C only.  Every population is read
-// from HBM once per step; the re-reads of halo columns and of the collided row
-// are served by L1/L2.
+// and marches down a chunk of H rows, two rows per iteration: every value a
+// thread handles is a float2 holding the same quantity on rows (2q, 2q+1) of
+// its column, and the arithmetic runs on Blackwell's packed FP32x2 units.  The
+// force needs rho within radius 2 of every node whose velocity is needed, and
+// the corrections need u, T within radius 1 of the collided node, so four
+// stages lag each other by one row pair.  For the leading pair q:
+//   A: rho, j (q)              pulled populations                 (W + 6 columns)
+//   B: Korteweg stress (q-1)   from rho of pairs q-2..q            (W + 4 columns)
+//   C: F, u, T, EOS (q-2)      div Pi of pairs q-3..q-1, Gamma     (W + 2 columns)
+//   D: collide (q-3)           Phi, q' from the fields of q-4..q-2 (W columns)
+// Fields shared between columns live in 3-deep shared-memory rings of row
+// pairs; the pulled f (stage A -> D), the pulled g (C -> D) and the centre
+// values (C -> D) of a column live in thread-private shared-memory rings.  The 6
+// halo columns of a strip belong to an extra warp that runs stages A-C only.
+// Loads of the next f and g rows are issued one iteration ahead.  Every
+// population is read from HBM once per step; re-reads of halo columns are
+// served by L2.
 #include "dispatch.h"
 
 namespace evlbm {
 
 namespace {
 
-constexpr int kW = 256;              // output columns per strip
-constexpr int kThreads = kW + 32;    // + one halo warp
-constexpr int kSlots = kW + 6;       // columns held per ring row
-constexpr int kRing = 4;
-constexpr int kFields = 11;          // rho, jx, jy, Pxx, Pxy, Pyy, ux, uy, flux_x, flux_y, wq
+// ---------------------------------------------------------------------------
+// Packed FP32x2 arithmetic.
+// ---------------------------------------------------------------------------
+typedef float2 v2;
+__device__ __forceinline__ v2 V(float a) { return make_float2(a, a); }
+__device__ __forceinline__ v2 V(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ v2 operator+(v2 a, v2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ v2 operator*(v2 a, v2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ v2 operator-(v2 a, v2 b) { return __ffma2_rn(b, V(-1.f), a); }
+__device__ __forceinline__ v2 operator-(v2 a) { return __fmul2_rn(a, V(-1.f)); }
+__device__ __forceinline__ v2 fma2(v2 a, v2 b, v2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ v2 rcp2(v2 a) { return V(__frcp_rn(a.x), __frcp_rn(a.y)); }
+// (lo.y, hi.x): the row pair shifted by one row.
+__device__ __forceinline__ v2 shift_up(v2 lo, v2 hi) { return V(lo.y, hi.x); }
+
+constexpr int kFields = 11;      // rho, jx, jy, Pxx, Pxy, Pyy, ux, uy, flux_x, flux_y, wq
+constexpr int kDepth = 3;        // ring depth (row pairs) of the shared fields
+constexpr int kCentre = 6;       // rho, Fx, Fy, RT, theta0, gamma0 handed from stage C to D
+
+// Strip of W output columns: W + 32 threads (the last warp owns the 6 halo
+// columns), MINB resident CTAs per SM requested from the compiler.
+template <int W> struct Shape;
+template <> struct Shape<64> { static constexpr int MINB = 4; };
+template <> struct Shape<96> { static constexpr int MINB = 2; };
+template <> struct Shape<128> { static constexpr int MINB = 2; };
+template <> struct Shape<192> { static constexpr int MINB = 1; };
+
+template <int W> constexpr int threads_of() { return W + 32; }
+template <int W> constexpr int slots_of() { return W + 6; }
+template <int W> constexpr size_t smem_of()
+{
+    return sizeof(v2) * (size_t)(kFields * kDepth * slots_of<W>() + (4 * 9 + 2 * 9 + 2 * kCentre) * W);
+}
 
 struct FusedArgs {
     const float *f, *g;
     float *fo, *go;
     const float *RT_iso;
     int nx, ny, nz, H;
-    unsigned N;                      // nodes of the lattice (Q*N < 2^31)
+    unsigned N;                  // nodes of the lattice (Q*N < 2^31)
     int eos;
     float a, b, kappa, lambda, c_eq, c_star;
 };
@@ -50,38 +81,47 @@ __device__ __forceinline__ int wrap_any(int v, int n)
     v %= n;
     return v < 0 ? v + n : v;
 }
-
 __device__ __forceinline__ int prev_row(int r, int ny) { return r == 0 ? ny - 1 : r - 1; }
 __device__ __forceinline__ int next_row(int r, int ny) { return r == ny - 1 ? 0 : r + 1; }
 
-// Loads the nine pulled populations of node (col, row): h_i = h~_i(x - c_i).
-// rows[k] = wrapped row y + (k - 1), cols[k] = wrapped column x + (k - 1).
-__device__ __forceinline__ void pull9(const float *__restrict__ base, unsigned N, const unsigned rowoff[3],
-                                      const int cols[3], float h[9])
+// Pulled populations of rows (r, r+1) of one column: h_i(y) = h~_i(x - c_ix, y - c_iy).
+// ro[k] = offset of wrapped row r - 1 + k (k = 0..3), cols[k] = wrapped column x - 1 + k.
+__device__ __forceinline__ void pull18(const float *__restrict__ base, unsigned N, const unsigned ro[4],
+                                       const int cols[3], v2 h[9])
 {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int cx = i % 3 - 1, cy = i / 3 - 1;
-        h[i] = __ldg(base + i * N + rowoff[1 - cy] + cols[1 - cx]);
+        const float *p = base + i * N + cols[1 - cx];
+        h[i] = V(__ldg(p + ro[1 - cy]), __ldg(p + ro[2 - cy]));
     }
 }
 
-template <bool THERMAL>
-__global__ void __launch_bounds__(kThreads, 2) k_fused2d(FusedArgs A)
+__device__ __forceinline__ v2 sum9(const v2 h[9])
 {
-    extern __shared__ float smem[];
-    auto ring = [&](int field, int row) -> float * { return smem + (field * kRing + (row & 3)) * kSlots; };
+    return ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+}
+
+template <int kW, bool THERMAL>
+__global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_fused2d(FusedArgs A)
+{
+    constexpr int S = slots_of<kW>();
+    extern __shared__ v2 smem[];
     enum { RHO, JX, JY, PXX, PXY, PYY, UX, UY, QX, QY, WQ };
+    auto fld = [&](int field, int slot3) -> v2 * { return smem + (field * kDepth + slot3) * S; };
+    v2 *const f9 = smem + kFields * kDepth * S;          // [4][9][kW]   pulled f, stage A -> D
+    v2 *const g9 = f9 + 4 * 9 * kW;                      // [2][9][kW]   pulled g, stage C -> D
+    v2 *const cen = g9 + 2 * 9 * kW;                     // [2][kCentre][kW]
 
     const int nx = A.nx, ny = A.ny;
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * kW;
     const int Weff = min(kW, nx - x0);
-    const int y0 = blockIdx.y * A.H;
+    const int y0 = blockIdx.y * A.H;                      // H is even
     const int Heff = min(A.H, ny - y0);
     const unsigned layer = (unsigned)blockIdx.z * (unsigned)nx * (unsigned)ny;
 
-    // Column role of this thread.
+    // Column role.
     int slot = 0, col = 0;
     bool inA = true, inB = true, inC = true, inD = true;
     if (t < kW) {
@@ -109,203 +149,295 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused2d(FusedArgs A)
 #pragma unroll
     for (int k = 0; k < 3; ++k) cols[k] = wrap_any(col - 1 + k, nx);
 
-    const float *fl = A.f + layer, *gl = A.g + layer;
-    float *fol = A.fo + layer, *gol = A.go + layer;
-    const unsigned N = A.N;
     const float a = A.a, b = A.b, kappa = A.kappa, lambda = A.lambda;
-    const float c_eq = A.c_eq, c_star = A.c_star;
+    const unsigned N = A.N;
+    auto rows4 = [&](int r, unsigned ro[4]) {      // rows r-1 .. r+2 of the layer
+        const int rp = next_row(r, ny);
+        ro[0] = layer + (unsigned)prev_row(r, ny) * nx;
+        ro[1] = layer + (unsigned)r * nx;
+        ro[2] = layer + (unsigned)rp * nx;
+        ro[3] = layer + (unsigned)next_row(rp, ny) * nx;
+    };
 
-    // Wrapped centre rows of the stages, advanced by one each iteration.
-    const int Lbeg = y0 - 3, Lend = y0 + Heff + 2;
-    int rA = wrap_any(Lbeg, ny);
-    int rC = wrap_any(Lbeg - 2, ny);
-    int rD = wrap_any(Lbeg - 3, ny);
+    // Pair indices: pair q holds rows 2q, 2q+1 (absolute, unwrapped).
+    const int q0 = y0 / 2;
+    const int qD_end = (y0 + Heff + 1) / 2;              // one past the last collided pair
+    const int qbeg = q0 - 3, qend = qD_end + 2;
+    int rA = wrap_any(2 * qbeg, ny);                      // wrapped first row of the next A pair
+    int rC = wrap_any(2 * (q0 - 1), ny);                  // ... of the next C pair
+    int rD = wrap_any(2 * q0, ny);                        // ... of the next D pair
+    int s0 = ((qbeg % 3) + 3) % 3;                        // ring slot of pair q
 
-    // Centre values of the row to be collided next (computed in stage C one
-    // iteration earlier), and its energy populations.
-    float cRho = 1.f, cFx = 0.f, cFy = 0.f, cUx = 0.f, cUy = 0.f, cRT = 0.f, cTh = 0.f, cP0 = 0.f, cG0 = 0.f;
-    float pRho = 1.f, pFx = 0.f, pFy = 0.f, pUx = 0.f, pUy = 0.f, pRT = 0.f, pTh = 0.f, pP0 = 0.f, pG0 = 0.f;
-    float gC[9], gN[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) gC[i] = gN[i] = 0.f;
+    v2 pf[9], pg[9];
+    if (inA) {
+        unsigned ro[4];
+        rows4(rA, ro);
+        pull18(A.f, N, ro, cols, pf);
+    }
+    if (THERMAL && inC) {
+        unsigned ro[4];
+        rows4(rC, ro);
+        pull18(A.g, N, ro, cols, pg);
+    }
 
-    for (int L = Lbeg; L <= Lend; ++L) {
-        // ---------------- A: rho, j of row L ----------------
+    for (int q = qbeg; q <= qend; ++q) {
+        const int sm1 = s0 == 0 ? 2 : s0 - 1;             // slot of q-1 (and of q-4)
+        const int sm2 = s0 == 2 ? 0 : s0 + 1;             // slot of q-2 (q-3 shares s0)
+        // ---------------- A: rho, j of pair q ----------------
         if (inA) {
-            const unsigned ro[3] = {(unsigned)prev_row(rA, ny) * nx, (unsigned)rA * nx, (unsigned)next_row(rA, ny) * nx};
-            float h[9];
-            pull9(fl, N, ro, cols, h);
-            const float rho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-            ring(RHO, L)[slot] = rho;
-            ring(JX, L)[slot] = ((h[2] + h[5]) + h[8]) - ((h[0] + h[3]) + h[6]);
-            ring(JY, L)[slot] = ((h[6] + h[7]) + h[8]) - ((h[0] + h[1]) + h[2]);
+            fld(RHO, s0)[slot] = sum9(pf);
+            fld(JX, s0)[slot] = ((pf[2] + pf[5]) + pf[8]) - ((pf[0] + pf[3]) + pf[6]);
+            fld(JY, s0)[slot] = ((pf[6] + pf[7]) + pf[8]) - ((pf[0] + pf[1]) + pf[2]);
+            if (inD) {
+                v2 *fr = f9 + (q & 3) * 9 * kW + t;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fr[i * kW] = pf[i];
+            }
+            rA = next_row(next_row(rA, ny), ny);
+            if (q < qend) {
+                unsigned ro[4];
+                rows4(rA, ro);
+                pull18(A.f, N, ro, cols, pf);
+            }
         }
-        rA = next_row(rA, ny);
         __syncthreads();
 
-        // ---------------- B: Korteweg stress of row L-1 ----------------
-        if (inB && L - 1 >= y0 - 2) {
-            const float *rs = ring(RHO, L - 2), *rc = ring(RHO, L - 1), *rn = ring(RHO, L);
-            const float SW = rs[slot - 1], S = rs[slot], SE = rs[slot + 1];
-            const float W_ = rc[slot - 1], C = rc[slot], E_ = rc[slot + 1];
-            const float NW = rn[slot - 1], Nn = rn[slot], NE = rn[slot + 1];
+        // ---------------- B: Korteweg stress of pair q-1 ----------------
+        if (inB && q - 1 >= q0 - 2) {
+            const v2 *r2 = fld(RHO, sm2), *r1 = fld(RHO, sm1), *r0 = fld(RHO, s0);
+            const v2 aW = r2[slot - 1], aC = r2[slot], aE = r2[slot + 1];     // pair q-2
+            const v2 bW = r1[slot - 1], bC = r1[slot], bE = r1[slot + 1];     // pair q-1 (centre rows)
+            const v2 cW = r0[slot - 1], cC = r0[slot], cE = r0[slot + 1];     // pair q
+            const v2 SW = shift_up(aW, bW), S_ = shift_up(aC, bC), SE = shift_up(aE, bE);
+            const v2 NW = shift_up(bW, cW), N_ = shift_up(bC, cC), NE = shift_up(bE, cE);
             // Isotropic D2Q9 stencils: grad = 3 sum w c phi, lap = 6 sum w (phi - phi_0).
-            const float dx = (1.f / 3.f) * (E_ - W_) + (1.f / 12.f) * ((NE - NW) + (SE - SW));
-            const float dy = (1.f / 3.f) * (Nn - S) + (1.f / 12.f) * ((NE + NW) - (SE + SW));
-            const float lap = (2.f / 3.f) * ((E_ + W_) + (Nn + S)) + (1.f / 6.f) * ((NE + NW) + (SE + SW)) -
-                              (10.f / 3.f) * C;
-            const float s = -a * C * C - kappa * C * lap - 0.5f * kappa * (dx * dx + dy * dy);
-            ring(PXX, L - 1)[slot] = s + kappa * dx * dx;
-            ring(PXY, L - 1)[slot] = kappa * dx * dy;
-            ring(PYY, L - 1)[slot] = s + kappa * dy * dy;
+            const v2 dx = fma2(V(1.f / 3.f), bE - bW, V(1.f / 12.f) * ((NE - NW) + (SE - SW)));
+            const v2 dy = fma2(V(1.f / 3.f), N_ - S_, V(1.f / 12.f) * ((NE + NW) - (SE + SW)));
+            const v2 lap = fma2(V(2.f / 3.f), (bE + bW) + (N_ + S_),
+                                fma2(V(1.f / 6.f), (NE + NW) + (SE + SW), V(-10.f / 3.f) * bC));
+            const v2 kdx = V(kappa) * dx, kdy = V(kappa) * dy;
+            // s = -a rho^2 - kappa rho lap - kappa/2 |grad rho|^2
+            const v2 s = -(fma2(V(a) * bC, bC, fma2(V(kappa) * bC, lap, V(0.5f) * fma2(kdx, dx, kdy * dy))));
+            fld(PXX, sm1)[slot] = fma2(kdx, dx, s);
+            fld(PXY, sm1)[slot] = kdx * dy;
+            fld(PYY, sm1)[slot] = fma2(kdy, dy, s);
         }
         __syncthreads();
 
-        // ---------------- C: force, velocity, temperature, EOS of row L-2 ----------------
-        if (inC && L - 2 >= y0 - 1) {
-            const float *xs = ring(PXX, L - 3), *xc = ring(PXX, L - 2), *xn = ring(PXX, L - 1);
-            const float *ys = ring(PXY, L - 3), *yc = ring(PXY, L - 2), *yn = ring(PXY, L - 1);
-            const float *zs = ring(PYY, L - 3), *zn = ring(PYY, L - 1);
-            const int sm = slot - 1, sp = slot + 1;
-            const float dxPxx = (1.f / 3.f) * (xc[sp] - xc[sm]) + (1.f / 12.f) * ((xn[sp] - xn[sm]) + (xs[sp] - xs[sm]));
-            const float dyPxy = (1.f / 3.f) * (yn[slot] - ys[slot]) + (1.f / 12.f) * ((yn[sp] + yn[sm]) - (ys[sp] + ys[sm]));
-            const float dxPxy = (1.f / 3.f) * (yc[sp] - yc[sm]) + (1.f / 12.f) * ((yn[sp] - yn[sm]) + (ys[sp] - ys[sm]));
-            const float dyPyy = (1.f / 3.f) * (zn[slot] - zs[slot]) + (1.f / 12.f) * ((zn[sp] + zn[sm]) - (zs[sp] + zs[sm]));
-            const float Fx = -(dxPxx + dyPxy), Fy = -(dxPxy + dyPyy);
-            const float rho = ring(RHO, L - 2)[slot];
-            const float ir = 1.f / rho;
-            const float ux = (ring(JX, L - 2)[slot] + 0.5f * Fx) * ir;
-            const float uy = (ring(JY, L - 2)[slot] + 0.5f * Fy) * ir;
-            float RT;
+        // ---------------- C: force, velocity, temperature, EOS of pair q-2 ----------------
+        if (inC && q - 2 >= q0 - 1) {
+            // Pi of pairs q-3 (slot s0), q-2 (sm2, centre rows), q-1 (sm1).
+            const int sw = slot - 1, se = slot + 1;
+            const v2 *x3 = fld(PXX, s0), *x2 = fld(PXX, sm2), *x1 = fld(PXX, sm1);
+            const v2 *y3 = fld(PXY, s0), *y2 = fld(PXY, sm2), *y1 = fld(PXY, sm1);
+            const v2 *z3 = fld(PYY, s0), *z2 = fld(PYY, sm2), *z1 = fld(PYY, sm1);
+            auto south = [&](const v2 *lo, const v2 *c, int k) { return shift_up(lo[k], c[k]); };
+            auto north = [&](const v2 *c, const v2 *hi, int k) { return shift_up(c[k], hi[k]); };
+            const v2 dxPxx = fma2(V(1.f / 3.f), x2[se] - x2[sw],
+                                  V(1.f / 12.f) * ((north(x2, x1, se) - north(x2, x1, sw)) +
+                                                   (south(x3, x2, se) - south(x3, x2, sw))));
+            const v2 yE = y2[se], yW = y2[sw];
+            const v2 yNE = north(y2, y1, se), yNW = north(y2, y1, sw), yN = north(y2, y1, slot);
+            const v2 ySE = south(y3, y2, se), ySW = south(y3, y2, sw), yS = south(y3, y2, slot);
+            const v2 dyPxy = fma2(V(1.f / 3.f), yN - yS, V(1.f / 12.f) * ((yNE + yNW) - (ySE + ySW)));
+            const v2 dxPxy = fma2(V(1.f / 3.f), yE - yW, V(1.f / 12.f) * ((yNE - yNW) + (ySE - ySW)));
+            const v2 dyPyy = fma2(V(1.f / 3.f), north(z2, z1, slot) - south(z3, z2, slot),
+                                  V(1.f / 12.f) * ((north(z2, z1, se) + north(z2, z1, sw)) -
+                                                   (south(z3, z2, se) + south(z3, z2, sw))));
+            const v2 Fx = -(dxPxx + dyPxy), Fy = -(dxPxy + dyPyy);
+            const v2 rho = fld(RHO, sm2)[slot];
+            const v2 ir = rcp2(rho);
+            const v2 ux = fma2(V(0.5f), Fx, fld(JX, sm2)[slot]) * ir;
+            const v2 uy = fma2(V(0.5f), Fy, fld(JY, sm2)[slot]) * ir;
+            v2 RT;
             if constexpr (THERMAL) {
-                const unsigned ro[3] = {(unsigned)prev_row(rC, ny) * nx, (unsigned)rC * nx,
-                                        (unsigned)next_row(rC, ny) * nx};
-                pull9(gl, N, ro, cols, gN);
-                const float Gam = ((gN[0] + gN[1]) + (gN[2] + gN[3])) + ((gN[4] + gN[5]) + (gN[6] + gN[7])) + gN[8];
-                const float E = (Gam + 0.5f * (ux * Fx + uy * Fy)) * ir;
-                RT = (2.f / 3.f) * (E - 0.5f * (ux * ux + uy * uy));
+                const v2 Gam = sum9(pg);
+                const v2 E = fma2(V(0.5f), fma2(ux, Fx, uy * Fy), Gam) * ir;
+                RT = V(2.f / 3.f) * fma2(V(-0.5f), fma2(ux, ux, uy * uy), E);
+                if (inD) {
+                    v2 *gr = g9 + (q & 1) * 9 * kW + t;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) gr[i * kW] = pg[i];
+                }
+                rC = next_row(next_row(rC, ny), ny);
+                if (q + 1 <= qend) {           // prefetch the next stage-C pair
+                    unsigned ro[4];
+                    rows4(rC, ro);
+                    pull18(A.g, N, ro, cols, pg);
+                }
             } else {
-                RT = __ldg(A.RT_iso + layer + (unsigned)rC * nx + cols[1]);
+                const float *Tp = A.RT_iso + layer + cols[1];
+                RT = V(__ldg(Tp + (unsigned)rC * nx), __ldg(Tp + (unsigned)next_row(rC, ny) * nx));
+                rC = next_row(next_row(rC, ny), ny);
             }
             // EOS in the Enskog gauge: P0 = P_E = rho RT Z, gamma0 = 1 + rho Z'/Z [+ 2/3 Z].
-            float Z, dlnZ;
+            v2 Z, dlnZ;
             if (A.eos == 0) {
-                Z = 1.f / (1.f - b * rho);
-                dlnZ = b * rho * Z;
+                const v2 br = V(b) * rho;
+                Z = rcp2(V(1.f) - br);
+                dlnZ = br * Z;
             } else {
-                const float eta = 0.25f * b * rho;
-                const float num = 1.f + eta * (1.f + eta * (1.f - eta));
-                const float iom = 1.f / (1.f - eta);
-                Z = num * iom * iom * iom;
-                dlnZ = eta * (4.f + eta * (4.f - 2.f * eta)) * iom / num;
+                const v2 eta = V(0.25f * b) * rho;
+                const v2 num = fma2(eta, fma2(eta, V(1.f) - eta, V(1.f)), V(1.f));
+                const v2 iom = rcp2(V(1.f) - eta);
+                Z = num * (iom * iom) * iom;
+                dlnZ = eta * fma2(eta, fma2(V(-2.f), eta, V(4.f)), V(4.f)) * iom * rcp2(num);
             }
-            const float g0 = THERMAL ? 1.f + dlnZ + (2.f / 3.f) * Z : 1.f + dlnZ;
-            const float th = RT * Z;
-            ring(UX, L - 2)[slot] = ux;
-            ring(UY, L - 2)[slot] = uy;
-            ring(QX, L - 2)[slot] = rho * ux * (ux * ux + 3.f * th - 1.f);
-            ring(QY, L - 2)[slot] = rho * uy * (uy * uy + 3.f * th - 1.f);
-            ring(WQ, L - 2)[slot] = th - RT;
-            // Centre values for the collision of this row at the next iteration.
-            cRho = rho; cFx = Fx; cFy = Fy; cUx = ux; cUy = uy; cRT = RT; cTh = th; cP0 = rho * th; cG0 = g0;
+            const v2 g0 = THERMAL ? fma2(V(2.f / 3.f), Z, V(1.f) + dlnZ) : V(1.f) + dlnZ;
+            const v2 th = RT * Z;
+            const v2 th3m1 = fma2(V(3.f), th, V(-1.f));
+            fld(UX, sm2)[slot] = ux;
+            fld(UY, sm2)[slot] = uy;
+            fld(QX, sm2)[slot] = rho * ux * fma2(ux, ux, th3m1);
+            fld(QY, sm2)[slot] = rho * uy * fma2(uy, uy, th3m1);
+            fld(WQ, sm2)[slot] = th - RT;
+            if (inD) {
+                v2 *cr = cen + (q & 1) * kCentre * kW + t;
+                cr[0 * kW] = rho; cr[1 * kW] = Fx; cr[2 * kW] = Fy;
+                cr[3 * kW] = RT; cr[4 * kW] = th; cr[5 * kW] = g0;
+            }
         }
-        rC = next_row(rC, ny);
         __syncthreads();
 
-        // ---------------- D: collide row L-3 ----------------
-        if (inD && L - 3 >= y0) {
-            // Values of row L-3 computed in stage C of the previous iteration.
-            const float rho = pRho, Fx = pFx, Fy = pFy, ux = pUx, uy = pUy, RT = pRT, th = pTh, P0 = pP0, g0 = pG0;
-            const int sm = slot - 1, sp = slot + 1;
-            const float *uxc = ring(UX, L - 3), *qxc = ring(QX, L - 3), *wqc = ring(WQ, L - 3);
-            const float *uys = ring(UY, L - 4), *uyn = ring(UY, L - 2);
-            const float *qys = ring(QY, L - 4), *qyn = ring(QY, L - 2);
-            const float *wqs = ring(WQ, L - 4), *wqn = ring(WQ, L - 2);
-            const float divu = 0.5f * (uxc[sp] - uxc[sm]) + 0.5f * (uyn[slot] - uys[slot]);
-            const float Phi1 = P0 * (5.f / 3.f - g0) * divu;
+        // ---------------- D: collide pair q-3 ----------------
+        if (inD && q - 3 >= q0) {
+            const int p = q - 3;                   // its stage C ran at iteration q-1
+            const v2 *cr = cen + ((q - 1) & 1) * kCentre * kW + t;
+            const v2 rho = cr[0], Fx = cr[kW], Fy = cr[2 * kW], RT = cr[3 * kW], th = cr[4 * kW], g0 = cr[5 * kW];
+            const int sw = slot - 1, se = slot + 1;
+            // fields of pairs p-1 (slot sm1), p (s0), p+1 (sm2)
+            const v2 *uxp = fld(UX, s0), *qxp = fld(QX, s0);
+            const v2 *uy4 = fld(UY, sm1), *uy3 = fld(UY, s0), *uy2 = fld(UY, sm2);
+            const v2 *qy4 = fld(QY, sm1), *qy3 = fld(QY, s0), *qy2 = fld(QY, sm2);
+            const v2 *w4 = fld(WQ, sm1), *w3 = fld(WQ, s0), *w2 = fld(WQ, sm2);
+            const v2 ux = uxp[slot], uy = uy3[slot];
+            const v2 qyc = qy3[slot], wqc = w3[slot];
+            const v2 uyN = shift_up(uy, uy2[slot]), uyS = shift_up(uy4[slot], uy);
+            const v2 qyN = shift_up(qyc, qy2[slot]), qyS = shift_up(qy4[slot], qyc);
+            const v2 wqN = shift_up(wqc, w2[slot]), wqS = shift_up(w4[slot], wqc);
+            const v2 P0 = rho * th;
+            const v2 divu = V(0.5f) * ((uxp[se] - uxp[sw]) + (uyN - uyS));
+            const v2 Phi1 = P0 * (V(5.f / 3.f) - g0) * divu;
             // Phi_aa = Phi' - d_a[rho u_a (u_a^2 + 3 theta0 - 1)] (sign cancelling the c^3 = c bias).
-            const float Phx = Phi1 - 0.5f * (qxc[sp] - qxc[sm]);
-            const float Phy = Phi1 - 0.5f * (qyn[slot] - qys[slot]);
-            const float lP0 = lambda * P0;
-            const float qx = lP0 * 0.5f * (wqc[sp] - wqc[sm]) + lambda * ux * Phi1;
-            const float qy = lP0 * 0.5f * (wqn[slot] - wqs[slot]) + lambda * uy * Phi1;
+            const v2 Phx = fma2(V(-0.5f), qxp[se] - qxp[sw], Phi1);
+            const v2 Phy = fma2(V(-0.5f), qyN - qyS, Phi1);
+            const v2 lP0h = V(0.5f * lambda) * P0, lPhi = V(lambda) * Phi1;
+            const v2 qx = fma2(lP0h, w3[se] - w3[sw], ux * lPhi);
+            const v2 qy = fma2(lP0h, wqN - wqS, uy * lPhi);
 
-            const float ir = 1.f / rho;
-            const float usx = ux + lambda * Fx * ir, usy = uy + lambda * Fy * ir;
-            const float zex = th + ux * ux, zey = th + uy * uy;
-            const float zsx = th + usx * usx + lambda * Phx * ir, zsy = th + usy * usy + lambda * Phy * ir;
+            const v2 lir = V(lambda) * rcp2(rho);
+            const v2 usx = fma2(Fx, lir, ux), usy = fma2(Fy, lir, uy);
+            const v2 zex = fma2(ux, ux, th), zey = fma2(uy, uy, th);
+            const v2 zpx = fma2(usx, usx, th), zpy = fma2(usy, usy, th);
+            const v2 zsx = fma2(Phx, lir, zpx), zsy = fma2(Phy, lir, zpy);
             // Psi factors (index 0, 1, 2 <-> c = -1, 0, +1), rho folded into the x factors.
-            const float ex[3] = {rho * 0.5f * (zex - ux), rho * (1.f - zex), rho * 0.5f * (zex + ux)};
-            const float ey[3] = {0.5f * (zey - uy), 1.f - zey, 0.5f * (zey + uy)};
-            const float sx[3] = {rho * 0.5f * (zsx - usx), rho * (1.f - zsx), rho * 0.5f * (zsx + usx)};
-            const float sy[3] = {0.5f * (zsy - usy), 1.f - zsy, 0.5f * (zsy + usy)};
+            const v2 hr = V(0.5f) * rho;
+            const v2 ex[3] = {hr * (zex - ux), rho - rho * zex, hr * (zex + ux)};
+            const v2 ey[3] = {V(0.5f) * (zey - uy), V(1.f) - zey, V(0.5f) * (zey + uy)};
+            const v2 sx[3] = {hr * (zsx - usx), rho - rho * zsx, hr * (zsx + usx)};
+            const v2 sy[3] = {V(0.5f) * (zsy - usy), V(1.f) - zsy, V(0.5f) * (zsy + usy)};
 
-            const unsigned ro[3] = {(unsigned)prev_row(rD, ny) * nx, (unsigned)rD * nx, (unsigned)next_row(rD, ny) * nx};
-            float h[9];
-            pull9(fl, N, ro, cols, h);
-            const float k_h = 1.f - c_eq, k_eq = c_eq - c_star;
-            const unsigned out = (unsigned)rD * nx + cols[1];
+            const v2 kh = V(1.f - A.c_eq), keq = V(A.c_eq - A.c_star), kst = V(A.c_star);
+            const unsigned out0 = layer + (unsigned)rD * nx + cols[1];
+            const unsigned out1 = layer + (unsigned)next_row(rD, ny) * nx + cols[1];
+            const bool second = 2 * p + 1 < y0 + Heff;
+            const v2 *fr = f9 + (p & 3) * 9 * kW + t;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const int ix = i % 3, iy = i / 3;
-                const float feq = ex[ix] * ey[iy];
-                const float fst = sx[ix] * sy[iy];
-                fol[i * N + out] = k_h * h[i] + k_eq * feq + c_star * fst;
+                const v2 o = fma2(kh, fr[i * kW], fma2(keq, ex[ix] * ey[iy], kst * (sx[ix] * sy[iy])));
+                A.fo[i * N + out0] = o.x;
+                if (second) A.fo[i * N + out1] = o.y;
             }
             if constexpr (THERMAL) {
                 // g^eq_i = rho [e PsiP_x PsiP_y + PsiS_x PsiP_y + PsiP_x PsiS_y], e = 3/2 RT,
                 // PsiP = Psi(u, theta0 + u^2), PsiS = Psi applied to (u^2/2, theta0 u + u^3/2,
-                // theta0^2 + 5/2 theta0 u^2 + u^4/2).
-                const float e = 1.5f * RT;
-                const float RTs = RT - (lambda * lambda / 3.f) * (Fx * Fx + Fy * Fy) * ir * ir;
-                const float es = 1.5f * RTs;
-                auto psiS = [&](float v, float out3[3]) {
-                    const float v2 = v * v;
-                    const float S0 = 0.5f * v2, S1 = v * (th + 0.5f * v2), S2 = th * th + v2 * (2.5f * th + 0.5f * v2);
-                    out3[0] = 0.5f * (S2 - S1);
-                    out3[1] = S0 - S2;
-                    out3[2] = 0.5f * (S2 + S1);
+                // theta0^2 + 5/2 theta0 u^2 + u^4/2); g* at (u*, RT* = RT - lambda^2 |F|^2/(3 rho^2)).
+                const v2 e = V(1.5f) * RT;
+                const v2 es = fma2(V(-0.5f), fma2(Fx, Fx, Fy * Fy) * (lir * lir), e);
+                auto psiS = [&](v2 v, v2 o3[3]) {
+                    const v2 vv = v * v;
+                    const v2 S0 = V(0.5f) * vv;
+                    const v2 S1 = v * fma2(V(0.5f), vv, th);
+                    const v2 S2 = fma2(th, th, vv * fma2(V(2.5f), th, S0));
+                    o3[0] = V(0.5f) * (S2 - S1);
+                    o3[1] = S0 - S2;
+                    o3[2] = V(0.5f) * (S2 + S1);
                 };
-                float Sx[3], Sy[3], SSx[3], SSy[3];
+                v2 Sx[3], Sy[3], SSx[3], SSy[3];
                 psiS(ux, Sx); psiS(uy, Sy); psiS(usx, SSx); psiS(usy, SSy);
                 // PsiP at the shifted velocity (no Phi: that correction belongs to f* only).
-                const float zpx = th + usx * usx, zpy = th + usy * usy;
-                const float px[3] = {rho * 0.5f * (zpx - usx), rho * (1.f - zpx), rho * 0.5f * (zpx + usx)};
-                const float py[3] = {0.5f * (zpy - usy), 1.f - zpy, 0.5f * (zpy + usy)};
-                float Ax[3], As[3];
+                const v2 px[3] = {hr * (zpx - usx), rho - rho * zpx, hr * (zpx + usx)};
+                const v2 py[3] = {V(0.5f) * (zpy - usy), V(1.f) - zpy, V(0.5f) * (zpy + usy)};
+                v2 Ax[3], As[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    Ax[k] = e * ex[k] + rho * Sx[k];      // rho (e PsiP_x + PsiS_x)
-                    As[k] = es * px[k] + rho * SSx[k];
+                    Ax[k] = fma2(e, ex[k], rho * Sx[k]);      // rho (e PsiP_x + PsiS_x)
+                    As[k] = fma2(es, px[k], rho * SSx[k]);
                 }
+                const v2 hqx = V(0.5f) * qx, hqy = V(0.5f) * qy;
+                const v2 *gr = g9 + (p & 1) * 9 * kW + t;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const int ix = i % 3, iy = i / 3;
-                    const float geq = Ax[ix] * ey[iy] + ex[ix] * Sy[iy];
-                    float gst = As[ix] * py[iy] + px[ix] * SSy[iy];
-                    if (i == 1) gst -= 0.5f * qy;     // c = (0,-1)
-                    if (i == 3) gst -= 0.5f * qx;     // c = (-1,0)
-                    if (i == 5) gst += 0.5f * qx;     // c = (1,0)
-                    if (i == 7) gst += 0.5f * qy;     // c = (0,1)
-                    gol[i * N + out] = k_h * gC[i] + k_eq * geq + c_star * gst;
+                    const v2 geq = fma2(Ax[ix], ey[iy], ex[ix] * Sy[iy]);
+                    v2 gst = fma2(As[ix], py[iy], px[ix] * SSy[iy]);
+                    if (i == 1) gst = gst - hqy;   // c = (0,-1)
+                    if (i == 3) gst = gst - hqx;   // c = (-1,0)
+                    if (i == 5) gst = gst + hqx;   // c = (1,0)
+                    if (i == 7) gst = gst + hqy;   // c = (0,1)
+                    const v2 o = fma2(kh, gr[i * kW], fma2(keq, geq, kst * gst));
+                    A.go[i * N + out0] = o.x;
+                    if (second) A.go[i * N + out1] = o.y;
                 }
             }
+            rD = next_row(next_row(rD, ny), ny);
         }
-        rD = next_row(rD, ny);
-        // The collision row of the next iteration is the one stage C just produced.
-        pRho = cRho; pFx = cFx; pFy = cFy; pUx = cUx; pUy = cUy; pRT = cRT; pTh = cTh; pP0 = cP0; pG0 = cG0;
-        if constexpr (THERMAL) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) gC[i] = gN[i];
-        }
+        s0 = sm2;                                          // slot of pair q+1
+    }
+}
+
+template <int W, bool THERMAL>
+cudaError_t launch_w(const FusedArgs &A, int nz, cudaStream_t st)
+{
+    static bool attr = false;
+    constexpr size_t smem = smem_of<W>();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused2d<W, THERMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid((A.nx + W - 1) / W, (A.ny + A.H - 1) / A.H, nz);
+    k_fused2d<W, THERMAL><<<grid, threads_of<W>(), smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <bool THERMAL>
+cudaError_t launch(int W, const FusedArgs &A, int nz, cudaStream_t st)
+{
+    switch (W) {
+    case 64: return launch_w<64, THERMAL>(A, nz, st);
+    case 96: return launch_w<96, THERMAL>(A, nz, st);
+    case 192: return launch_w<192, THERMAL>(A, nz, st);
+    default: return launch_w<128, THERMAL>(A, nz, st);
     }
 }
 
 }  // namespace
 
+const int kFusedWidths[kFusedWidthCount] = {64, 96, 128, 192};
+
 bool fused2d_supported(int prec, int Q, const KParams &p)
 {
     return prec == 1 && Q == 9 && p.force_form == 0 && (long long)9 * p.N < (1LL << 31);
+}
+
+void fused2d_default_tile(const KParams &p, int *W, int *H)
+{
+    *W = p.nx >= 128 ? 128 : (p.nx > 64 ? 96 : 64);
+    const int h = p.ny <= 128 ? p.ny : 128;
+    *H = h + (h & 1);
 }
 
 cudaError_t fused2d_step(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
@@ -329,25 +461,10 @@ cudaError_t fused2d_step(int prec, const KParams &p, const void *f, const void *
     A.lambda = float(p.lambda);
     A.c_eq = float(p.c_eq);
     A.c_star = float(p.c_star);
-    A.H = p.ny <= 128 ? p.ny : 128;
-    const size_t smem = sizeof(float) * kFields * kRing * kSlots;
-    const dim3 grid((p.nx + kW - 1) / kW, (p.ny + A.H - 1) / A.H, p.nz);
-    if (p.thermal) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_fused2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
-        }
-        k_fused2d<true><<<grid, kThreads, smem, st>>>(A);
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_fused2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
-        }
-        k_fused2d<false><<<grid, kThreads, smem, st>>>(A);
-    }
-    return cudaGetLastError();
+    int W = p.tile_w, H = p.tile_h;
+    if (W <= 0 || H <= 0) fused2d_default_tile(p, &W, &H);
+    A.H = H + (H & 1);                 // row pairs: chunks of an even number of rows
+    return p.thermal ? launch<true>(W, A, p.nz, st) : launch<false>(W, A, p.nz, st);
 }
 
 }  // namespace evlbm
