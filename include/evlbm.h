@@ -164,6 +164,27 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  * (no convergence within the iteration limit). */
 int lbm_coexistence(int eos, double a, double b, double RT, double out[2]);
 
+/* One FP64 time step that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory while
+ * they run -- for example code executing where cudaMalloc is not allowed, or
+ * an application whose device memory is pre-planned by another allocator.  The
+ * caller owns every buffer: d_f, d_g (input populations, [Q][N] FP64 on the
+ * device), d_RT (the frozen R*T field [N], read only when thermal = 0; d_g and
+ * d_g_out are ignored then) and d_f_out, d_g_out (output populations; must not
+ * alias the inputs).  The intermediate fields live in a static array inside the
+ * library sized for at most 32768 nodes (7.5 MiB, held on every GPU that loads
+ * the library until the process exits); larger lattices return LBM_EINVAL.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.  All
+ * calls share the one array, so calls whose kernels overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.  The
+ * populations are bit-identical to lbm_step on an LBM_FP64 context.
+ * params->precision must be LBM_FP64.  Asynchronous on `stream`.
+ * Errors: LBM_EINVAL (bad parameters, NULL buffers, too many nodes), LBM_ECUDA. */
+int lbm_step_noalloc(const lbm_params *params, const double *d_f, const double *d_g, const double *d_RT,
+                     double *d_f_out, double *d_g_out, void *stream);
+
 /* Critical point (rho_c, RT_c) of p = P_E - a rho^2 (host computation). */
 int lbm_critical_point(int eos, double a, double b, double out[2]);
 

@@ -18,7 +18,7 @@ __all__ = [
     "lbm_params", "lib", "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_device",
     "lbm_populations", "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_set_tile",
     "lbm_get_tile", "lbm_autotune", "lbm_sync", "lbm_free",
-    "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "LBMError", "Lattice",
+    "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "lbm_step_noalloc", "LBMError", "Lattice",
     "LBM_D2Q9", "LBM_D3Q27", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
     "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS",
 ]
@@ -36,6 +36,7 @@ EXPORTED_SYMBOLS = (
     "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_populations",
     "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_set_tile", "lbm_get_tile",
     "lbm_autotune", "lbm_sync", "lbm_free", "lbm_last_error", "lbm_coexistence", "lbm_critical_point",
+    "lbm_step_noalloc",
 )
 
 
@@ -107,6 +108,7 @@ def lib():
             L.lbm_last_error.restype = ctypes.c_char_p
             L.lbm_coexistence.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.lbm_critical_point.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+            L.lbm_step_noalloc.argtypes = [pp, vp, vp, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -232,6 +234,16 @@ def lbm_critical_point(eos, a, b):
     if rc != LBM_OK:
         raise LBMError(rc, "lbm_critical_point")
     return float(out[0]), float(out[1])
+
+
+def lbm_step_noalloc(params: lbm_params, d_f, d_g, d_RT, d_f_out, d_g_out, stream=0):
+    """One FP64 step on caller-owned device buffers (pointers as ints, 0 = NULL);
+    allocates nothing (see include/evlbm.h)."""
+    vp = ctypes.c_void_p
+    rc = lib().lbm_step_noalloc(ctypes.byref(params), vp(d_f or None), vp(d_g or None), vp(d_RT or None),
+                                vp(d_f_out or None), vp(d_g_out or None), vp(stream or None))
+    if rc != LBM_OK:
+        raise LBMError(rc, "lbm_step_noalloc")
 
 
 class Lattice:

@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(HERE, "..", "include")]
 # Per-file extra flags.
-EXTRA = {"ref_f64.cu": ["--fmad=false"]}
+EXTRA = {"ref_f64.cu": ["--fmad=false"], "noalloc.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:
