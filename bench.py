@@ -32,6 +32,9 @@ TRS = (0.7, 0.8, 0.9)
 RADII = (64.0, 128.0, 256.0)
 A, B, KAPPA, TAU = 0.1, 4.0, 0.116, 0.3
 BYTES_PER_LU = 2 * 9 * 2 * 4          # D2Q9, f and g, read + write, FP32
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_fused2d launch on this workload
+# (profiles/fused2d_d2q9_thermal_fp32.md); None whenever the kernel changes.
+MEASURED_TRAFFIC_BYTES = 1.3398e9
 WORKLOAD = "droplet Laplace sweep: 9 x 1024^2 D2Q9 thermal, FP32"
 
 
@@ -262,7 +265,8 @@ def run(args):
                    "tile": {"w": tile[0], "h": tile[1], "autotuned": not (args.no_autotune or args.tile)},
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (MEASURED_TRAFFIC_BYTES / 1e9 if nz == 9 else None), "traffic_unit": "GB per launch",
                      "note": f"{BYTES_PER_LU} algorithmic B/LU; peak {peak_kind} copy bandwidth"},
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -272,6 +276,58 @@ def run(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ensemble(args):
+    """512 independent 2-D droplet-pair domains of uneven sizes (64..512 per side), FP32
+    thermal, all advanced by one persistent launch per call under a CUDA graph."""
+    import torch
+
+    import paper_2508_00577_gb300 as ev
+    from paper_2508_00577_gb300 import inputs
+
+    _, Tc = ev.lbm_critical_point(1, A, B)
+    doms = inputs.ensemble_domains(args.domains)
+    cache = {}
+    rho, u, T, sizes = [], [], [], []
+    for dm in doms:
+        tr = round(dm["tr"], 3)
+        if tr not in cache:
+            cache[tr] = ev.lbm_coexistence(1, A, B, tr * Tc)
+        rv, rl = cache[tr]
+        r, v, t = inputs.two_droplets(dm["nx"], dm["ny"], dm["r1"], dm["r2"], dm["gap"], rv, rl, dm["tr"] * Tc)
+        rho.append(r); u.append(v); T.append(t); sizes.append((dm["nx"], dm["ny"]))
+    params = ev.lbm_params.make(eos=ev.LBM_EOS_CS, a=A, b=B, kappa=KAPPA, tau=TAU, thermal=1, precision=ev.LBM_FP32)
+    stream = torch.cuda.Stream()
+    bt = ev.Batch(params, sizes, rho, u, T, stream=stream.cuda_stream)
+    tile = bt.autotune(1)
+    bt.step(args.warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        bt.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    N = bt.nodes()
+    value = N * args.steps / (ms * 1e-3) / 1e6
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_LU * N * args.steps / (ms * 1e-3) / 1e9
+    finite = all(np.isfinite(bt.moments(d)[0]).all() for d in (0, len(sizes) // 2, len(sizes) - 1))
+    bt.close()
+    print(json.dumps({
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"ensemble: {len(sizes)} uneven D2Q9 thermal domains (64..512)^2, FP32, "
+                               "one persistent launch per call under a CUDA graph",
+                   "nodes": N, "tile": {"w": tile[0], "h": tile[1], "autotuned": True}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "note": f"{BYTES_PER_LU} algorithmic B/LU; peak {peak_kind}"},
+        "clocks": clk.summary(), "gpu_launches": 1, "finite": bool(finite),
+    }), flush=True)
     return 0
 
 
@@ -285,9 +341,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed launch shape W,H of the fused kernel")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble"],
+                    help="sweep: the headline droplet Laplace sweep; ensemble: 512 uneven domains")
+    ap.add_argument("--domains", type=int, default=512)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
     return run(args)
 
 

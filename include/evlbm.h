@@ -185,6 +185,60 @@ int lbm_coexistence(int eos, double a, double b, double RT, double out[2]);
 int lbm_step_noalloc(const lbm_params *params, const double *d_f, const double *d_g, const double *d_RT,
                      double *d_f_out, double *d_g_out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched ensembles: many independent periodic 2-D domains of uneven sizes
+ * (D2Q9, FP32, divergence-form force), advanced together by one persistent
+ * kernel per lbm_batch_step call, launched from a captured CUDA graph.  Each
+ * domain follows exactly the same step as lbm_step (Eq. pre_LBM etc.); with the
+ * same launch shape its populations are bit-identical to a single context's.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+/* Create a batch of n_domains >= 1 domains of nx[d] x ny[d] nodes sharing the
+ * physics of `common` (lattice LBM_D2Q9, precision LBM_FP32, force_form 0,
+ * nz 1; common->nx/ny are ignored).  HOST fields are concatenated in domain
+ * order: rho[sum N_d], T[sum N_d], and u as the domains' [2][N_d] blocks one
+ * after the other.  `stream` is a cudaStream_t; NULL makes the batch create and
+ * own a non-blocking stream (the legacy default stream cannot be captured).
+ * Errors: LBM_EINVAL, LBM_ENONFINITE, LBM_ENOMEM, LBM_ECUDA. */
+int lbm_batch_init(const lbm_params *common, int n_domains, const int *nx, const int *ny, const double *rho,
+                   const double *u, const double *T, void *stream, lbm_batch **out);
+
+/* Advance every domain by n_steps >= 0 steps in one persistent launch.  Work
+ * items (step, domain, tile) are taken in step-major order; an item waits, with
+ * a bounded spin, for its domain's previous step.  Synchronises the stream.
+ * Errors: LBM_EINVAL, LBM_ECUDA, LBM_ETIMEOUT (a wait gave up; the state is then
+ * partially advanced and should be re-initialised, the batch stays usable). */
+int lbm_batch_step(lbm_batch *b, int n_steps);
+
+/* Macroscopic fields of one domain (as lbm_moments): rho[N_d], u[2][N_d], T[N_d]
+ * (host FP64; any may be NULL).  Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */
+int lbm_batch_moments(lbm_batch *b, int domain, double *rho, double *u, double *T);
+
+/* Launch shape of the tiles (as lbm_set_tile; tile_w in 64, 96, 128, 192). */
+int lbm_batch_set_tile(lbm_batch *b, int tile_w, int tile_h);
+int lbm_batch_get_tile(const lbm_batch *b, int *tile_w, int *tile_h);
+
+/* Autotuner: times every launch shape for probe_steps single-step launches that
+ * read the current state and write the spare buffer (state unchanged); keeps
+ * the fastest.  Errors: LBM_EINVAL, LBM_ECUDA, LBM_ETIMEOUT. */
+int lbm_batch_autotune(lbm_batch *b, int probe_steps, int *tile_w, int *tile_h);
+
+/* Failure detection: polls (>= 1) a step wait may spin before it gives up
+ * (default 2^24, about 2 s).  probe_unset_flag = 1 makes every item also wait on
+ * a device flag that nothing sets, so that the next lbm_batch_step reports
+ * LBM_ETIMEOUT (used to test the error path); 0 turns it off. */
+int lbm_batch_set_wait_limit(lbm_batch *b, long long polls, int probe_unset_flag);
+
+/* Total nodes of the batch (-1 for NULL). */
+long long lbm_batch_nodes(const lbm_batch *b);
+
+/* Release the batch.  NULL is accepted. */
+int lbm_batch_free(lbm_batch *b);
+
+/* Last error message of the batch ("" if none). */
+const char *lbm_batch_last_error(const lbm_batch *b);
+
 /* Critical point (rho_c, RT_c) of p = P_E - a rho^2 (host computation). */
 int lbm_critical_point(int eos, double a, double b, double out[2]);
 

@@ -20,7 +20,7 @@ __all__ = [
     "lbm_get_tile", "lbm_autotune", "lbm_sync", "lbm_free",
     "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "lbm_step_noalloc", "LBMError", "Lattice",
     "LBM_D2Q9", "LBM_D3Q27", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
-    "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS",
+    "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS", "Batch",
 ]
 
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENOMEM, LBM_ENONFINITE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5
@@ -36,7 +36,9 @@ EXPORTED_SYMBOLS = (
     "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_populations",
     "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_set_tile", "lbm_get_tile",
     "lbm_autotune", "lbm_sync", "lbm_free", "lbm_last_error", "lbm_coexistence", "lbm_critical_point",
-    "lbm_step_noalloc",
+    "lbm_step_noalloc", "lbm_batch_init", "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_tile",
+    "lbm_batch_get_tile", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_batch_nodes",
+    "lbm_batch_free", "lbm_batch_last_error",
 )
 
 
@@ -109,6 +111,18 @@ def lib():
             L.lbm_coexistence.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.lbm_critical_point.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
             L.lbm_step_noalloc.argtypes = [pp, vp, vp, vp, vp, vp, vp]
+            L.lbm_batch_init.argtypes = [pp, ctypes.c_int, ip, ip, dp, dp, dp, vp, ctypes.POINTER(vp)]
+            L.lbm_batch_step.argtypes = [vp, ctypes.c_int]
+            L.lbm_batch_moments.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+            L.lbm_batch_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            L.lbm_batch_get_tile.argtypes = [vp, ip, ip]
+            L.lbm_batch_autotune.argtypes = [vp, ctypes.c_int, ip, ip]
+            L.lbm_batch_set_wait_limit.argtypes = [vp, ctypes.c_longlong, ctypes.c_int]
+            L.lbm_batch_nodes.argtypes = [vp]
+            L.lbm_batch_nodes.restype = ctypes.c_longlong
+            L.lbm_batch_free.argtypes = [vp]
+            L.lbm_batch_last_error.argtypes = [vp]
+            L.lbm_batch_last_error.restype = ctypes.c_char_p
             _lib = L
     return _lib
 
@@ -244,6 +258,82 @@ def lbm_step_noalloc(params: lbm_params, d_f, d_g, d_RT, d_f_out, d_g_out, strea
                                 vp(d_f_out or None), vp(d_g_out or None), vp(stream or None))
     if rc != LBM_OK:
         raise LBMError(rc, "lbm_step_noalloc")
+
+
+def _bcheck(rc, b):
+    if rc != LBM_OK:
+        msg = lib().lbm_batch_last_error(b) if b else b""
+        raise LBMError(rc, msg.decode() if msg else "")
+
+
+class Batch:
+    """Batched ensemble of independent 2-D domains (lbm_batch_* of the C ABI)."""
+
+    def __init__(self, params: lbm_params, sizes, rho, u, T, stream=0):
+        """sizes: [(nx, ny), ...]; rho, T: per-domain flat arrays; u: per-domain [2][N_d] arrays."""
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        n = len(self.sizes)
+        nx = (ctypes.c_int * n)(*[s[0] for s in self.sizes])
+        ny = (ctypes.c_int * n)(*[s[1] for s in self.sizes])
+        rho_c = np.ascontiguousarray(np.concatenate([np.ravel(r) for r in rho]), dtype=np.float64)
+        u_c = np.ascontiguousarray(np.concatenate([np.ravel(v) for v in u]), dtype=np.float64)
+        T_c = np.ascontiguousarray(np.concatenate([np.ravel(t) for t in T]), dtype=np.float64)
+        total = sum(a * b for a, b in self.sizes)
+        if rho_c.size != total or T_c.size != total or u_c.size != 2 * total:
+            raise ValueError("field sizes do not match the domain sizes")
+        out = ctypes.c_void_p()
+        rc = lib().lbm_batch_init(ctypes.byref(params), n, nx, ny, _dptr(rho_c), _dptr(u_c), _dptr(T_c),
+                                  ctypes.c_void_p(stream), ctypes.byref(out))
+        _bcheck(rc, None)
+        self.params = params
+        self.b = out.value
+
+    def step(self, n=1):
+        _bcheck(lib().lbm_batch_step(self.b, int(n)), self.b)
+        return self
+
+    def moments(self, d):
+        nx, ny = self.sizes[d]
+        N = nx * ny
+        rho, u, T = np.zeros(N), np.zeros(2 * N), np.zeros(N)
+        _bcheck(lib().lbm_batch_moments(self.b, int(d), _dptr(rho), _dptr(u), _dptr(T)), self.b)
+        return rho, u.reshape(2, N), T
+
+    def set_tile(self, w, h):
+        _bcheck(lib().lbm_batch_set_tile(self.b, int(w), int(h)), self.b)
+
+    def get_tile(self):
+        w, h = ctypes.c_int(), ctypes.c_int()
+        _bcheck(lib().lbm_batch_get_tile(self.b, ctypes.byref(w), ctypes.byref(h)), self.b)
+        return w.value, h.value
+
+    def autotune(self, probe_steps=2):
+        w, h = ctypes.c_int(), ctypes.c_int()
+        _bcheck(lib().lbm_batch_autotune(self.b, int(probe_steps), ctypes.byref(w), ctypes.byref(h)), self.b)
+        return w.value, h.value
+
+    def set_wait_limit(self, polls, probe_unset_flag=0):
+        _bcheck(lib().lbm_batch_set_wait_limit(self.b, int(polls), int(probe_unset_flag)), self.b)
+
+    def nodes(self):
+        return lib().lbm_batch_nodes(self.b)
+
+    def close(self):
+        if self.b:
+            lib().lbm_batch_free(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Lattice:

@@ -130,10 +130,10 @@ struct Eos {
 
 // Root of a monotone function on [lo, hi] by bisection (fixed number of halvings).
 template <typename Fn>
-__device__ double bisect(Fn fn, double lo, double hi)
+__device__ double bisect(Fn fn, double lo, double hi, int halvings)
 {
     double flo = fn(lo);
-    for (int k = 0; k < 200; ++k) {
+    for (int k = 0; k < halvings; ++k) {
         const double mid = 0.5 * (lo + hi), fm = fn(mid);
         if ((flo <= 0.0) == (fm <= 0.0)) {
             lo = mid;
@@ -150,20 +150,25 @@ __global__ void k_coexistence(Eos E, double rho_c, double *out, int *status)
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double rmax = E.rho_max() * (1.0 - 1e-12);
     // Spinodal densities: dp/drho = 0 on either side of the critical density.
-    const double s1 = bisect([&](double r) { return E.dp(r); }, 1e-12 * rho_c, rho_c);
-    const double s2 = bisect([&](double r) { return E.dp(r); }, rho_c, rmax);
+    const double s1 = bisect([&](double r) { return E.dp(r); }, 1e-12 * rho_c, rho_c, 80);
+    const double s2 = bisect([&](double r) { return E.dp(r); }, rho_c, rmax, 80);
     if (!(E.dp(0.5 * (s1 + s2)) < 0.0)) {
         *status = 1;   // no van der Waals loop: above the critical temperature
         return;
     }
+    // Pressure level with equal chemical potentials, by bisection to 1e-9 relative,
+    // then Newton on (p(rho_l) - p(rho_v), mu(rho_l) - mu(rho_v)).
     double Plo = fmax(E.p(s2), 0.0), Phi = E.p(s1), rv = 0.0, rl = 0.0;
-    for (int k = 0; k < 200; ++k) {
+    for (int k = 0; k < 100 && Phi - Plo > 1e-9 * Phi; ++k) {
         const double P = 0.5 * (Plo + Phi);
-        rv = bisect([&](double r) { return E.p(r) - P; }, 1e-300, s1);
-        rl = bisect([&](double r) { return E.p(r) - P; }, s2, rmax);
+        rv = bisect([&](double r) { return E.p(r) - P; }, 1e-300, s1, 64);
+        rl = bisect([&](double r) { return E.p(r) - P; }, s2, rmax, 64);
         if (E.mu(rl) < E.mu(rv)) Phi = P;   // liquid favoured: above saturation
         else Plo = P;
     }
+    const double P = 0.5 * (Plo + Phi);
+    rv = bisect([&](double r) { return E.p(r) - P; }, 1e-300, s1, 64);
+    rl = bisect([&](double r) { return E.p(r) - P; }, s2, rmax, 64);
     int it = 0;
     for (; it < 100; ++it) {
         const double F1 = E.p(rl) - E.p(rv), F2 = E.mu(rl) - E.mu(rv);
@@ -175,7 +180,7 @@ __global__ void k_coexistence(Eos E, double rho_c, double *out, int *status)
         const double dl = (-F2 * J11 + F1 * J21) / det;
         rv += dv;
         rl += dl;
-        if (fabs(dv) <= 1e-13 * rv && fabs(dl) <= 1e-13 * rl) break;
+        if (fabs(dv) <= 1e-14 * rv && fabs(dl) <= 1e-14 * rl) break;
     }
     out[0] = rv;
     out[1] = rl;
