@@ -20,6 +20,7 @@ struct lbm_ctx {
     size_t pop_bytes;      // bytes per stored population
     size_t real_bytes;     // bytes per scratch value (8 for FP64, 4 otherwise)
     void *f[2], *g[2];
+    void *R[2];            // per-node reference states of 16-bit storage ([D + 3][N])
     int cur;
     void *RT_iso;          // frozen R*T field (thermal = 0), in the scratch precision
     void *scratch;         // stage-kernel fields, allocated on first use
@@ -80,8 +81,8 @@ int validate(const lbm_params *p)
     return LBM_OK;
 }
 
-// Fills the kernel parameter block; rho_ref/E_ref are the deviation references.
-void fill_kparams(lbm_ctx *c, double rho_ref, double E_ref)
+// Fills the kernel parameter block.
+void fill_kparams(lbm_ctx *c)
 {
     const lbm_params &p = c->P;
     KParams &k = c->K;
@@ -100,15 +101,9 @@ void fill_kparams(lbm_ctx *c, double rho_ref, double E_ref)
     const double beta = 1.0 / (2.0 * p.tau + 1.0);   // Eq. (beta), dt = 1
     k.c_eq = 2.0 * beta;
     k.c_star = (1.0 / p.lambda) * (1.0 - beta);      // (dt/lambda)(1 - beta)
-    k.rho_ref = rho_ref;
-    k.E_ref = E_ref;
-    const bool dev = p.precision == LBM_FP16_DEV || p.precision == LBM_BF16_DEV;
-    for (int i = 0; i < c->Q; ++i) {
-        const double w = evlbm::w_of(i, c->Q);
-        k.foff[i] = dev ? float(w * rho_ref) : 0.0f;
-        k.goff[i] = dev ? float(w * rho_ref * E_ref) : 0.0f;
-    }
 }
+
+bool dev16(const lbm_ctx *c) { return c->P.precision == LBM_FP16_DEV || c->P.precision == LBM_BF16_DEV; }
 
 int run_macro(lbm_ctx *c)
 {
@@ -117,7 +112,7 @@ int run_macro(lbm_ctx *c)
     cudaError_t e = fp64(c) ? evlbm::ref_macro_f64(c->Q, c->K, c->scratch, c->RT_iso, c->f[c->cur], c->g[c->cur],
                                                   c->stream)
                             : evlbm::ref_macro_f32(c->P.precision, c->Q, c->K, c->scratch, c->RT_iso,
-                                                   c->f[c->cur], c->g[c->cur], c->stream);
+                                                   c->f[c->cur], c->g[c->cur], c->R[c->cur], c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "moment stages");
     return LBM_OK;
 }
@@ -146,6 +141,7 @@ void free_all(lbm_ctx *c)
     for (int k = 0; k < 2; ++k) {
         if (c->f[k]) cudaFree(c->f[k]);
         if (c->g[k]) cudaFree(c->g[k]);
+        if (c->R[k]) cudaFree(c->R[k]);
     }
     if (c->RT_iso) cudaFree(c->RT_iso);
     if (c->scratch) cudaFree(c->scratch);
@@ -178,8 +174,7 @@ int lbm_init(const lbm_params *params, const double *rho, const double *u, const
     const long long N = c->N;
     const int D = c->D;
 
-    // Host-side checks of the initial fields and the deviation references.
-    double rsum = 0.0, esum = 0.0;
+    // Host-side checks of the initial fields.
     for (long long n = 0; n < N; ++n) {
         if (!(rho[n] > 0.0) || !isfinite(rho[n]) || !(T[n] > 0.0) || !isfinite(T[n])) {
             free(c);
@@ -190,10 +185,8 @@ int lbm_init(const lbm_params *params, const double *rho, const double *u, const
                 free(c);
                 return fail(nullptr, LBM_ENONFINITE, "u must be finite (node %lld)", n);
             }
-        rsum += rho[n];
-        esum += 1.5 * params->R * T[n];
     }
-    fill_kparams(c, rsum / double(N), esum / double(N));
+    fill_kparams(c);
 
     // Device state.
     const size_t pop = c->pop_bytes * (size_t)c->Q * (size_t)N;
@@ -201,6 +194,7 @@ int lbm_init(const lbm_params *params, const double *rho, const double *u, const
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         e = cudaMalloc(&c->f[k], pop);
         if (e == cudaSuccess && params->thermal) e = cudaMalloc(&c->g[k], pop);
+        if (e == cudaSuccess && dev16(c)) e = cudaMalloc(&c->R[k], 2 * (size_t)(D + 3) * (size_t)N);
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->red, evlbm::totals_work_bytes(N));
     if (e == cudaSuccess) e = cudaMalloc(&c->RT_iso, c->real_bytes * (size_t)N);
@@ -237,7 +231,7 @@ int lbm_init(const lbm_params *params, const double *rho, const double *u, const
     if (e == cudaSuccess)
         e = fp64(c) ? evlbm::ref_init_f64(c->Q, c->K, d_rho, d_u, d_RT, c->f[0], c->g[0], c->stream)
                     : evlbm::ref_init_f32(params->precision, c->Q, c->K, d_rho, d_u, d_RT, c->f[0], c->g[0],
-                                          c->stream);
+                                          c->R[0], c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d_fields);
     if (e != cudaSuccess) {
@@ -271,7 +265,7 @@ int lbm_step(lbm_ctx *c, int n_steps)
                                     c->g[nx], c->stream);
         else
             e = evlbm::ref_step_f32(c->P.precision, c->Q, c->K, c->scratch, c->RT_iso, c->f[c->cur], c->g[c->cur],
-                                    c->f[nx], c->g[nx], c->stream);
+                                    c->f[nx], c->g[nx], c->R[c->cur], c->R[nx], c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step");
         c->cur = nx;
         c->steps++;
@@ -318,8 +312,8 @@ int lbm_populations(lbm_ctx *c, double *f, double *g)
     double *tmp = nullptr;
     CK(c, cudaMalloc(&tmp, sizeof(double) * cnt));
     for (int which = 0; which < (c->P.thermal && g ? 2 : 1); ++which) {
-        cudaError_t e = evlbm::expand_f32(c->P.precision, c->Q, c->K, which ? c->g[c->cur] : c->f[c->cur], tmp, which,
-                                          c->stream);
+        cudaError_t e = evlbm::expand_f32(c->P.precision, c->Q, c->K, which ? c->g[c->cur] : c->f[c->cur],
+                                          c->R[c->cur], tmp, which, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(which ? g : f, tmp, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -336,7 +330,8 @@ int lbm_conserved(lbm_ctx *c, double out[5])
 {
     if (!c || !out) return c ? fail(c, LBM_EINVAL, "out is NULL") : LBM_EINVAL;
     int bad = 0;
-    cudaError_t e = evlbm::totals(c->P.precision, c->Q, c->K, c->f[c->cur], c->g[c->cur], c->red, out, &bad, c->stream);
+    cudaError_t e = evlbm::totals(c->P.precision, c->Q, c->K, c->f[c->cur], c->g[c->cur], c->R[c->cur], c->red, out,
+                                  &bad, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_conserved");
     if (bad) return fail(c, LBM_ENONFINITE, "non-finite population after %lld steps", c->steps);
     return LBM_OK;

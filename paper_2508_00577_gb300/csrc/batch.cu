@@ -218,7 +218,6 @@ struct lbm_batch {
     long long graph_limit;
     void *scratch;               // stage-kernel fields for lbm_batch_moments (largest domain)
     long long max_nodes;
-    float rho_ref_unused;
     long long steps;
     KParams K;                   // common physics (per-domain sizes filled on use)
     char err[512];
@@ -267,7 +266,7 @@ int retile(lbm_batch *b)
     return LBM_OK;
 }
 
-BatchArgs make_args(const lbm_batch *b, int n_steps, bool from_cur, bool into_spare)
+BatchArgs make_args(const lbm_batch *b, int n_steps)
 {
     BatchArgs B;
     memset(&B, 0, sizeof(B));
@@ -276,8 +275,6 @@ BatchArgs make_args(const lbm_batch *b, int n_steps, bool from_cur, bool into_sp
     B.popA_g = b->g[c];
     B.popB_f = b->f[c ^ 1];
     B.popB_g = b->g[c ^ 1];
-    (void)from_cur;
-    (void)into_spare;
     B.RT_iso = b->RT_iso;
     B.dom = b->d_dom;
     B.n_domains = b->n;
@@ -304,7 +301,7 @@ cudaError_t enqueue(lbm_batch *b, int n_steps)
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_error, 0, sizeof(int), b->stream);
     if (e != cudaSuccess) return e;
-    const BatchArgs B = make_args(b, n_steps, true, true);
+    const BatchArgs B = make_args(b, n_steps);
     const int grid = b->P.thermal ? evlbm::grid_for<true>(b->tile_w) : evlbm::grid_for<false>(b->tile_w);
     if (grid <= 0) return cudaErrorLaunchOutOfResources;
     return b->P.thermal ? evlbm::launch_batch<true>(b->tile_w, B, grid, b->stream)
@@ -488,7 +485,7 @@ int lbm_batch_init(const lbm_params *p, int n_domains, const int *nx, const int 
         const KParams K = domain_kparams(b, d);
         if (e == cudaSuccess)
             e = evlbm::ref_init_f32(1, 9, K, d_fields, d_fields + Nd, d_fields + 3 * Nd, b->f[0] + b->dom[d].off,
-                                    p->thermal ? b->g[0] + b->dom[d].off : nullptr, b->stream);
+                                    p->thermal ? b->g[0] + b->dom[d].off : nullptr, nullptr, b->stream);
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->RT_iso, rt.data(), sizeof(float) * nodes, cudaMemcpyHostToDevice, b->stream);
@@ -602,7 +599,7 @@ int lbm_batch_moments(lbm_batch *b, int domain, double *rho, double *u, double *
     const BatchDomain &D = b->dom[domain];
     const long long Nd = K.N;
     cudaError_t e = evlbm::ref_macro_f32(1, 9, K, b->scratch, b->RT_iso + D.foff, b->f[b->cur] + D.off,
-                                         b->P.thermal ? b->g[b->cur] + D.off : nullptr, b->stream);
+                                         b->P.thermal ? b->g[b->cur] + D.off : nullptr, nullptr, b->stream);
     if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_moments: %s", cudaGetErrorString(e));
     std::vector<float> h(4 * Nd);
     using O = evlbm::FieldOffsets;

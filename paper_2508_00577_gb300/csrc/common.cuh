@@ -19,11 +19,7 @@ struct KParams {
     double a, b, kappa, lambda;
     double c_eq;         // 2 beta
     double c_star;       // (dt/lambda)(1 - beta)
-    double rho_ref;      // reference density of deviation storage
-    double E_ref;        // reference energy of deviation storage
     int tile_w, tile_h;  // launch shape of the fused kernel (0 = default)
-    float foff[27];      // deviation offsets w_i rho_ref (0 for FP32/FP64 storage)
-    float goff[27];      // deviation offsets w_i rho_ref E_ref
 };
 
 // Velocity set: i = (cx+1) + 3(cy+1) + 9(cz+1).
@@ -59,11 +55,14 @@ template <> struct Store<float> {
 };
 template <> struct Store<__half> {
     static constexpr bool dev = true;
+    // Value after a round trip through the storage format (registers only).
+    __device__ static __forceinline__ float round(float v) { return __half2float(__float2half_rn(v)); }
     __device__ static __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
     __device__ static __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     static constexpr bool dev = true;
+    __device__ static __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
     __device__ static __forceinline__ float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };

@@ -17,16 +17,19 @@ cudaError_t ref_export_f64(int Q, const KParams &p, void *scratch, double R, flo
                            cudaStream_t st);
 cudaError_t expand_f64(int Q, const KParams &p, const void *src, double *dst, int which, cudaStream_t st);
 
-// Stage kernels in FP32; storage 1 = FP32, 2 = FP16 deviations, 3 = BF16 deviations.
+// Stage kernels in FP32; storage 1 = FP32, 2 = FP16, 3 = BF16.  16-bit storage holds
+// deviations from each node's own local equilibrium plus that node's reference
+// state R ([D + 3][N] in the same format, double-buffered: Rin read, Rout written).
 cudaError_t ref_init_f32(int prec, int Q, const KParams &p, const void *rho, const void *u, const void *RT, void *f,
-                         void *g, cudaStream_t st);
+                         void *g, void *Rout, cudaStream_t st);
 cudaError_t ref_macro_f32(int prec, int Q, const KParams &p, void *scratch, const void *RT_iso, const void *f,
-                          const void *g, cudaStream_t st);
+                          const void *g, const void *Rin, cudaStream_t st);
 cudaError_t ref_step_f32(int prec, int Q, const KParams &p, void *scratch, const void *RT_iso, const void *f,
-                         const void *g, void *fo, void *go, cudaStream_t st);
+                         const void *g, void *fo, void *go, const void *Rin, void *Rout, cudaStream_t st);
 cudaError_t ref_export_f32(int Q, const KParams &p, void *scratch, double R, float *rho, float *u, float *T,
                            cudaStream_t st);
-cudaError_t expand_f32(int prec, int Q, const KParams &p, const void *src, double *dst, int which, cudaStream_t st);
+cudaError_t expand_f32(int prec, int Q, const KParams &p, const void *src, const void *R, double *dst, int which,
+                       cudaStream_t st);
 
 // Scratch layout of the stage kernels: rho, j, Gam, Pi, lap, A, F, u, RT, theta0, P0, gamma0, flux, wq.
 constexpr int kRefFieldCount = 30;
@@ -48,8 +51,8 @@ cudaError_t fused2d_step(int prec, const KParams &p, const void *f, const void *
 // FP64 totals of the state (mass, momentum x/y/z, energy) and a non-finite flag.
 // `work` must hold at least totals_work_bytes(N) bytes.
 size_t totals_work_bytes(long long N);
-cudaError_t totals(int prec, int Q, const KParams &p, const void *f, const void *g, void *work, double *h_out,
-                   int *h_nonfinite, cudaStream_t st);
+cudaError_t totals(int prec, int Q, const KParams &p, const void *f, const void *g, const void *R, void *work,
+                   double *h_out, int *h_nonfinite, cudaStream_t st);
 
 // Maxwell construction in FP64 on the GPU.
 cudaError_t coexistence(int eos, double a, double b, double RT, double rho_c, double *h_out, int *h_status);

@@ -2,6 +2,7 @@
 // construction of the coexisting densities.
 #include <math.h>
 #include "dispatch.h"
+#include "ref_kernels.cuh"
 
 namespace evlbm {
 
@@ -10,20 +11,12 @@ namespace {
 constexpr int kRedBlocks = 608;   // 4 x 152 SMs
 constexpr int kRedThreads = 256;
 
-template <typename S>
-__device__ __forceinline__ double pop64(const S *p, float off)
-{
-    if constexpr (Store<S>::dev)
-        return double(off) + double(Store<S>::load(p));
-    else
-        return double(Store<S>::load(p));
-}
-
 // Each thread sums its nodes in ascending order, the block combines the threads
-// in a fixed tree; the result does not depend on scheduling.
+// in a fixed tree; the result does not depend on scheduling.  16-bit storage is
+// expanded with the node's reference equilibrium first.
 template <typename S, int Q>
-__global__ void __launch_bounds__(kRedThreads) k_totals_partial(KParams p, const S *f, const S *g, double *partial,
-                                                                 int *nonfinite)
+__global__ void __launch_bounds__(kRedThreads) k_totals_partial(KParams p, const S *f, const S *g, const S *R,
+                                                                 double *partial, int *nonfinite)
 {
     __shared__ double sh[5][kRedThreads];
     double acc[5] = {0, 0, 0, 0, 0};
@@ -31,9 +24,12 @@ __global__ void __launch_bounds__(kRedThreads) k_totals_partial(KParams p, const
     const long long N = p.N;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
+        RefState<float> r{};
+        if constexpr (Store<S>::dev) r = load_ref<float, S, Q>(R, N, n);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double fi = pop64<S>(f + i * N + n, p.foff[i]);
+            double fi = double(Store<S>::load(f + i * N + n));
+            if constexpr (Store<S>::dev) fi = double(ref_f<float, Q>(i, r) + fscale<float, Q>(i, r) * float(fi));
             bad |= !isfinite(fi);
             acc[0] += fi;
             const int c[3] = {cx_of(i), cy_of(i), cz_of(i, Q)};
@@ -41,7 +37,8 @@ __global__ void __launch_bounds__(kRedThreads) k_totals_partial(KParams p, const
             for (int a = 0; a < 3; ++a)
                 acc[1 + a] += c[a] == 1 ? fi : (c[a] == -1 ? -fi : 0.0);
             if (p.thermal) {
-                const double gi = pop64<S>(g + i * N + n, p.goff[i]);
+                double gi = double(Store<S>::load(g + i * N + n));
+                if constexpr (Store<S>::dev) gi = double(ref_g<float, Q>(i, r) + gscale<float, Q>(i, r) * float(gi));
                 bad |= !isfinite(gi);
                 acc[4] += gi;
             }
@@ -81,7 +78,8 @@ __global__ void k_totals_final(const double *partial, double *out)
 }
 
 template <typename S>
-cudaError_t totals_s(int Q, const KParams &p, const void *f, const void *g, void *work, cudaStream_t st)
+cudaError_t totals_s(int Q, const KParams &p, const void *f, const void *g, const void *R, void *work,
+                     cudaStream_t st)
 {
     double *partial = static_cast<double *>(work);
     double *out = partial + 5 * kRedBlocks;
@@ -89,11 +87,11 @@ cudaError_t totals_s(int Q, const KParams &p, const void *f, const void *g, void
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     if (Q == 9)
-        k_totals_partial<S, 9><<<kRedBlocks, kRedThreads, 0, st>>>(p, static_cast<const S *>(f),
-                                                                  static_cast<const S *>(g), partial, flag);
+        k_totals_partial<S, 9><<<kRedBlocks, kRedThreads, 0, st>>>(
+            p, static_cast<const S *>(f), static_cast<const S *>(g), static_cast<const S *>(R), partial, flag);
     else
-        k_totals_partial<S, 27><<<kRedBlocks, kRedThreads, 0, st>>>(p, static_cast<const S *>(f),
-                                                                   static_cast<const S *>(g), partial, flag);
+        k_totals_partial<S, 27><<<kRedBlocks, kRedThreads, 0, st>>>(
+            p, static_cast<const S *>(f), static_cast<const S *>(g), static_cast<const S *>(R), partial, flag);
     k_totals_final<<<1, 1024, 0, st>>>(partial, out);
     return cudaGetLastError();
 }
@@ -191,15 +189,15 @@ __global__ void k_coexistence(Eos E, double rho_c, double *out, int *status)
 
 size_t totals_work_bytes(long long) { return sizeof(double) * (5 * kRedBlocks + 8) + 64; }
 
-cudaError_t totals(int prec, int Q, const KParams &p, const void *f, const void *g, void *work, double *h_out,
-                   int *h_nonfinite, cudaStream_t st)
+cudaError_t totals(int prec, int Q, const KParams &p, const void *f, const void *g, const void *R, void *work,
+                   double *h_out, int *h_nonfinite, cudaStream_t st)
 {
     cudaError_t e;
     switch (prec) {
-    case 0: e = totals_s<double>(Q, p, f, g, work, st); break;
-    case 1: e = totals_s<float>(Q, p, f, g, work, st); break;
-    case 2: e = totals_s<__half>(Q, p, f, g, work, st); break;
-    default: e = totals_s<__nv_bfloat16>(Q, p, f, g, work, st); break;
+    case 0: e = totals_s<double>(Q, p, f, g, R, work, st); break;
+    case 1: e = totals_s<float>(Q, p, f, g, R, work, st); break;
+    case 2: e = totals_s<__half>(Q, p, f, g, R, work, st); break;
+    default: e = totals_s<__nv_bfloat16>(Q, p, f, g, R, work, st); break;
     }
     if (e != cudaSuccess) return e;
     double *out = static_cast<double *>(work) + 5 * kRedBlocks;

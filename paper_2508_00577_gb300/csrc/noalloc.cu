@@ -77,8 +77,8 @@ extern "C" int lbm_step_noalloc(const lbm_params *p, const double *d_f, const do
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = p->lattice == LBM_D2Q9
                         ? evlbm::ref_step_t<double, double, 9>(k, g_scratch_addr[dev], d_RT, d_f, d_g, d_f_out,
-                                                               d_g_out, st)
+                                                               d_g_out, nullptr, nullptr, st)
                         : evlbm::ref_step_t<double, double, 27>(k, g_scratch_addr[dev], d_RT, d_f, d_g, d_f_out,
-                                                                d_g_out, st);
+                                                                d_g_out, nullptr, nullptr, st);
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }

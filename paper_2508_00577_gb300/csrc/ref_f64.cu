@@ -10,22 +10,22 @@ namespace evlbm {
 cudaError_t ref_init_f64(int Q, const KParams &p, const void *rho, const void *u, const void *RT, void *f, void *g,
                          cudaStream_t st)
 {
-    return EVLBM_Q_SWITCH(Q, (ref_init_t<double, double, 9>(p, rho, u, RT, f, g, st)),
-                          (ref_init_t<double, double, 27>(p, rho, u, RT, f, g, st)));
+    return EVLBM_Q_SWITCH(Q, (ref_init_t<double, double, 9>(p, rho, u, RT, f, g, nullptr, st)),
+                          (ref_init_t<double, double, 27>(p, rho, u, RT, f, g, nullptr, st)));
 }
 
 cudaError_t ref_macro_f64(int Q, const KParams &p, void *scratch, const void *RT_iso, const void *f, const void *g,
                           cudaStream_t st)
 {
-    return EVLBM_Q_SWITCH(Q, (ref_macro_t<double, double, 9>(p, scratch, RT_iso, f, g, st)),
-                          (ref_macro_t<double, double, 27>(p, scratch, RT_iso, f, g, st)));
+    return EVLBM_Q_SWITCH(Q, (ref_macro_t<double, double, 9>(p, scratch, RT_iso, f, g, nullptr, st)),
+                          (ref_macro_t<double, double, 27>(p, scratch, RT_iso, f, g, nullptr, st)));
 }
 
 cudaError_t ref_step_f64(int Q, const KParams &p, void *scratch, const void *RT_iso, const void *f, const void *g,
                          void *fo, void *go, cudaStream_t st)
 {
-    return EVLBM_Q_SWITCH(Q, (ref_step_t<double, double, 9>(p, scratch, RT_iso, f, g, fo, go, st)),
-                          (ref_step_t<double, double, 27>(p, scratch, RT_iso, f, g, fo, go, st)));
+    return EVLBM_Q_SWITCH(Q, (ref_step_t<double, double, 9>(p, scratch, RT_iso, f, g, fo, go, nullptr, nullptr, st)),
+                          (ref_step_t<double, double, 27>(p, scratch, RT_iso, f, g, fo, go, nullptr, nullptr, st)));
 }
 
 cudaError_t ref_export_f64(int Q, const KParams &p, void *scratch, double R, float *rho, float *u, float *T,
@@ -37,8 +37,8 @@ cudaError_t ref_export_f64(int Q, const KParams &p, void *scratch, double R, flo
 
 cudaError_t expand_f64(int Q, const KParams &p, const void *src, double *dst, int which, cudaStream_t st)
 {
-    return EVLBM_Q_SWITCH(Q, (expand_t<double, 9>(p, src, dst, which, st)),
-                          (expand_t<double, 27>(p, src, dst, which, st)));
+    return EVLBM_Q_SWITCH(Q, (expand_t<double, 9>(p, src, nullptr, dst, which, st)),
+                          (expand_t<double, 27>(p, src, nullptr, dst, which, st)));
 }
 
 }  // namespace evlbm

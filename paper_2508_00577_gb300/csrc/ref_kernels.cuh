@@ -24,22 +24,60 @@ __host__ __device__ constexpr int c_of(int i, int a, int Q)
     return a == 0 ? cx_of(i) : (a == 1 ? cy_of(i) : cz_of(i, Q));
 }
 
-template <typename real, typename S>
-__device__ __forceinline__ real ldpop(const S *p, float off)
+// ---------------------------------------------------------------------------
+// 16-bit storage.  A node stores its populations as deviations from its own
+// local equilibrium, delta_i(x) = h~_i(x) - h^eq_i(R(x)), next to the reference
+// R(x) = (rho, u, theta0, RT) of that node in the same 16-bit format.  The
+// reference is rounded to 16 bits before it is used on either side, so a puller
+// reconstructs exactly the value the writer meant: h_i(y) = h^eq_i(R(y - c_i)) +
+// delta_i(y - c_i).  FP32/FP64 storage holds the populations themselves.
+// ---------------------------------------------------------------------------
+template <typename real> struct RefState {
+    real rho, u[3], th, RT;
+};
+
+template <typename S> __device__ __forceinline__ float ld16(const S *p) { return Store<S>::load(p); }
+
+// R layout: [D + 3][N] = rho, u_x, u_y, (u_z), theta0, RT.
+template <typename real, typename S, int Q>
+__device__ __forceinline__ RefState<real> load_ref(const S *R, long long N, long long n)
 {
-    if constexpr (Store<S>::dev)
-        return real(off) + real(Store<S>::load(p));
-    else
-        return real(Store<S>::load(p));
+    constexpr int D = (Q == 9) ? 2 : 3;
+    RefState<real> r;
+    r.rho = real(ld16<S>(R + n));
+    r.u[0] = r.u[1] = r.u[2] = real(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) r.u[a] = real(ld16<S>(R + (1 + a) * N + n));
+    r.th = real(ld16<S>(R + (1 + D) * N + n));
+    r.RT = real(ld16<S>(R + (2 + D) * N + n));
+    return r;
 }
 
-template <typename real, typename S>
-__device__ __forceinline__ void stpop(S *p, real v, float off)
+// Rounds a state to the 16-bit format (what load_ref will return after store_ref).
+template <typename real, typename S, int Q>
+__device__ __forceinline__ RefState<real> round_ref(real rho, const real *u, real th, real RT)
 {
-    if constexpr (Store<S>::dev)
-        Store<S>::store(p, float(v - real(off)));
-    else
-        Store<S>::store(p, v);
+    constexpr int D = (Q == 9) ? 2 : 3;
+    auto r16 = [](real v) { return real(Store<S>::round(float(v))); };
+    RefState<real> r;
+    r.rho = r16(rho);
+    r.u[0] = r.u[1] = r.u[2] = real(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) r.u[a] = r16(u[a]);
+    r.th = r16(th);
+    r.RT = r16(RT);
+    return r;
+}
+
+template <typename real, typename S, int Q>
+__device__ __forceinline__ void store_ref(S *R, long long N, long long n, const RefState<real> &r)
+{
+    constexpr int D = (Q == 9) ? 2 : 3;
+    Store<S>::store(R + n, float(r.rho));
+#pragma unroll
+    for (int a = 0; a < D; ++a) Store<S>::store(R + (1 + a) * N + n, float(r.u[a]));
+    Store<S>::store(R + (1 + D) * N + n, float(r.th));
+    Store<S>::store(R + (2 + D) * N + n, float(r.RT));
 }
 
 struct Node {
@@ -183,6 +221,32 @@ __device__ __forceinline__ real geq_i(int i, real rho, const real *u, real theta
     return rho * (e * pP + sS);
 }
 
+// Scales of the stored deviations: w_i rho_r for f, w_i rho_r (3/2 RT_r) for g.  They
+// keep the stored numbers near 1e-3..1, inside FP16's normal range.
+template <typename real, int Q>
+__device__ __forceinline__ real fscale(int i, const RefState<real> &r) { return real(w_of(i, Q)) * r.rho; }
+template <typename real, int Q>
+__device__ __forceinline__ real gscale(int i, const RefState<real> &r)
+{
+    return real(w_of(i, Q)) * r.rho * (real(1.5) * r.RT);
+}
+
+// Equilibria of a reference state (population i).
+template <typename real, int Q>
+__device__ __forceinline__ real ref_f(int i, const RefState<real> &r)
+{
+    real z[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < Lat<Q>::D; ++a) z[a] = r.th + r.u[a] * r.u[a];
+    return prod_eq<real, Q>(i, r.rho, r.u, z);
+}
+
+template <typename real, int Q>
+__device__ __forceinline__ real ref_g(int i, const RefState<real> &r)
+{
+    return geq_i<real, Q>(i, r.rho, r.u, r.th, r.RT);
+}
+
 // ---------------------------------------------------------------------------
 // Scratch fields of the stage kernels (each [N] unless noted).
 // ---------------------------------------------------------------------------
@@ -195,7 +259,7 @@ template <typename real> struct RefFields {
 
 // Initial populations f = f^eq(rho, u, theta0(rho, RT)), g = g^eq(rho, u, RT).
 template <typename real, typename S, int Q>
-__global__ void k_init(KParams p, const real *rho_in, const real *u_in, const real *RT_in, S *f, S *g)
+__global__ void k_init(KParams p, const real *rho_in, const real *u_in, const real *RT_in, S *f, S *g, S *Rout)
 {
     Node nd;
     if (!node_of(p, nd)) return;
@@ -211,30 +275,65 @@ __global__ void k_init(KParams p, const real *rho_in, const real *u_in, const re
         u[a] = u_in[a * N + n];
         zeta[a] = theta0 + u[a] * u[a];
     }
+    RefState<real> ref{};
+    if constexpr (Store<S>::dev) {
+        ref = round_ref<real, S, Q>(rho, u, theta0, RT);
+        store_ref<real, S, Q>(Rout, N, n, ref);
+    }
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-        stpop<real, S>(f + i * N + n, prod_eq<real, Q>(i, rho, u, zeta), p.foff[i]);
+    for (int i = 0; i < Q; ++i) {
+        const real v = prod_eq<real, Q>(i, rho, u, zeta);
+        if constexpr (Store<S>::dev)
+            Store<S>::store(f + i * N + n, float((v - ref_f<real, Q>(i, ref)) / fscale<real, Q>(i, ref)));
+        else Store<S>::store(f + i * N + n, v);
+    }
     if (p.thermal) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-            stpop<real, S>(g + i * N + n, geq_i<real, Q>(i, rho, u, theta0, RT), p.goff[i]);
+        for (int i = 0; i < Q; ++i) {
+            const real v = geq_i<real, Q>(i, rho, u, theta0, RT);
+            if constexpr (Store<S>::dev)
+                Store<S>::store(g + i * N + n, float((v - ref_g<real, Q>(i, ref)) / gscale<real, Q>(i, ref)));
+            else Store<S>::store(g + i * N + n, v);
+        }
+    }
+}
+
+// Pulled populations h_i(x) = h~_i(x - c_i) of one node, f and (thermal) g.
+template <typename real, typename S, int Q>
+__device__ __forceinline__ void pull_node(const KParams &p, const Node &nd, const S *f, const S *g, const S *Rin,
+                                          real *fo, real *go)
+{
+    const long long N = p.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const long long src = shifted(p, nd, -cx_of(i), -cy_of(i), -cz_of(i, Q));
+        if constexpr (Store<S>::dev) {
+            const RefState<real> r = load_ref<real, S, Q>(Rin, N, src);
+            fo[i] = ref_f<real, Q>(i, r) + fscale<real, Q>(i, r) * real(Store<S>::load(f + i * N + src));
+            if (p.thermal)
+                go[i] = ref_g<real, Q>(i, r) + gscale<real, Q>(i, r) * real(Store<S>::load(g + i * N + src));
+        } else {
+            fo[i] = real(Store<S>::load(f + i * N + src));
+            if (p.thermal) go[i] = real(Store<S>::load(g + i * N + src));
+        }
     }
 }
 
 // Stages 1-2: pull streaming f_i(x) = f~_i(x - c_i) and the raw moments
 // rho = sum f_i, j_a = sum c_ia f_i, Gamma = sum g_i (ascending i).
 template <typename real, typename S, int Q>
-__global__ void k_moments(KParams p, const S *f, const S *g, RefFields<real> w)
+__global__ void k_moments(KParams p, const S *f, const S *g, const S *Rin, RefFields<real> w)
 {
     Node nd;
     if (!node_of(p, nd)) return;
     constexpr int D = Lat<Q>::D;
     const long long N = p.N, n = nd.n;
+    real fs[Q], gs[Q];
+    pull_node<real, S, Q>(p, nd, f, g, Rin, fs, gs);
     real rho = real(0.0), j[3] = {real(0.0), real(0.0), real(0.0)}, Gam = real(0.0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const long long src = shifted(p, nd, -cx_of(i), -cy_of(i), -cz_of(i, Q));
-        const real fi = ldpop<real, S>(f + i * N + src, p.foff[i]);
+        const real fi = fs[i];
         rho = rho + fi;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -242,7 +341,7 @@ __global__ void k_moments(KParams p, const S *f, const S *g, RefFields<real> w)
             if (c == 1) j[a] = j[a] + fi;
             else if (c == -1) j[a] = j[a] - fi;
         }
-        if (p.thermal) Gam = Gam + ldpop<real, S>(g + i * N + src, p.goff[i]);
+        if (p.thermal) Gam = Gam + gs[i];
     }
     w.rho[n] = rho;
 #pragma unroll
@@ -341,7 +440,8 @@ __global__ void k_macro(KParams p, RefFields<real> w)
 // correction_q), equilibria (Eqs. feq, f_star, geq, gstar, g_corr) and the
 // collision h~ = h + 2 beta (h^eq - h) + (dt/lambda)(1 - beta)(h* - h^eq).
 template <typename real, typename S, int Q>
-__global__ void k_collide(KParams p, RefFields<real> w, const S *f_src, const S *g_src, S *f_dst, S *g_dst)
+__global__ void k_collide(KParams p, RefFields<real> w, const S *f_src, const S *g_src, S *f_dst, S *g_dst,
+                          const S *Rin, S *Rout)
 {
     Node nd;
     if (!node_of(p, nd)) return;
@@ -374,13 +474,22 @@ __global__ void k_collide(KParams p, RefFields<real> w, const S *f_src, const S 
         zeq[d] = theta0 + u[d] * u[d];
         zs[d] = theta0 + us[d] * us[d] + lambda * Phi[d] / rho;
     }
+    real fs[Q], gs[Q];
+    pull_node<real, S, Q>(p, nd, f_src, g_src, Rin, fs, gs);
+    RefState<real> ref{};
+    if constexpr (Store<S>::dev) {
+        ref = round_ref<real, S, Q>(rho, u, theta0, RT);
+        store_ref<real, S, Q>(Rout, N, n, ref);
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const long long src = shifted(p, nd, -cx_of(i), -cy_of(i), -cz_of(i, Q));
-        const real h = ldpop<real, S>(f_src + i * N + src, p.foff[i]);
+        const real h = fs[i];
         const real feq = prod_eq<real, Q>(i, rho, u, zeq);
         const real fst = prod_eq<real, Q>(i, rho, us, zs);
-        stpop<real, S>(f_dst + i * N + n, h + c_eq * (feq - h) + c_star * (fst - feq), p.foff[i]);
+        const real v = h + c_eq * (feq - h) + c_star * (fst - feq);
+        if constexpr (Store<S>::dev)
+            Store<S>::store(f_dst + i * N + n, float((v - ref_f<real, Q>(i, ref)) / fscale<real, Q>(i, ref)));
+        else Store<S>::store(f_dst + i * N + n, v);
     }
     if (p.thermal) {
         real FF = real(0.0);
@@ -389,8 +498,7 @@ __global__ void k_collide(KParams p, RefFields<real> w, const S *f_src, const S 
         const real RTs = RT - lambda * lambda / (real(3.0) * rho * rho) * FF;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const long long src = shifted(p, nd, -cx_of(i), -cy_of(i), -cz_of(i, Q));
-            const real h = ldpop<real, S>(g_src + i * N + src, p.goff[i]);
+            const real h = gs[i];
             const real geq = geq_i<real, Q>(i, rho, u, theta0, RT);
             real gst = geq_i<real, Q>(i, rho, us, theta0, RTs);
             const int c2 = cx_of(i) * cx_of(i) + cy_of(i) * cy_of(i) + cz_of(i, Q) * cz_of(i, Q);
@@ -404,7 +512,10 @@ __global__ void k_collide(KParams p, RefFields<real> w, const S *f_src, const S 
                 }
                 gst = gst + real(0.5) * cq;
             }
-            stpop<real, S>(g_dst + i * N + n, h + c_eq * (geq - h) + c_star * (gst - geq), p.goff[i]);
+            const real v = h + c_eq * (geq - h) + c_star * (gst - geq);
+            if constexpr (Store<S>::dev)
+                Store<S>::store(g_dst + i * N + n, float((v - ref_g<real, Q>(i, ref)) / gscale<real, Q>(i, ref)));
+            else Store<S>::store(g_dst + i * N + n, v);
         }
     }
 }
@@ -424,20 +535,23 @@ __global__ void k_export_f32(KParams p, RefFields<real> w, double R, float *rho,
         for (int d = 0; d < D; ++d) u[d * N + n] = float(w.u[d * N + n]);
 }
 
-// Populations expanded to FP64 (deviation storage adds the offsets back).
+// Post-collision populations expanded to FP64 (16-bit storage adds the node's
+// reference equilibrium back).
 template <typename S, int Q>
-__global__ void k_expand(KParams p, const S *src, double *dst, int which)
+__global__ void k_expand(KParams p, const S *src, const S *R, double *dst, int which)
 {
     Node nd;
     if (!node_of(p, nd)) return;
     const long long N = p.N, n = nd.n;
+    RefState<float> r{};
+    if constexpr (Store<S>::dev) r = load_ref<float, S, Q>(R, N, n);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float off = which == 0 ? p.foff[i] : p.goff[i];
+        double v = double(Store<S>::load(src + i * N + n));
         if constexpr (Store<S>::dev)
-            dst[i * N + n] = double(off) + double(Store<S>::load(src + i * N + n));
-        else
-            dst[i * N + n] = double(Store<S>::load(src + i * N + n));
+            v = which == 0 ? double(ref_f<float, Q>(i, r) + fscale<float, Q>(i, r) * float(v))
+                           : double(ref_g<float, Q>(i, r) + gscale<float, Q>(i, r) * float(v));
+        dst[i * N + n] = v;
     }
 }
 

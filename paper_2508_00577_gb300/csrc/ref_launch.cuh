@@ -34,24 +34,25 @@ inline dim3 node_grid(long long N, int block) { return dim3((unsigned)((N + bloc
 
 template <typename real, typename S, int Q>
 cudaError_t ref_init_t(const KParams &p, const void *rho, const void *u, const void *RT, void *f, void *g,
-                       cudaStream_t st)
+                       void *Rout, cudaStream_t st)
 {
     const int B = 256;
     k_init<real, S, Q><<<node_grid(p.N, B), B, 0, st>>>(p, static_cast<const real *>(rho),
                                                         static_cast<const real *>(u),
                                                         static_cast<const real *>(RT), static_cast<S *>(f),
-                                                        static_cast<S *>(g));
+                                                        static_cast<S *>(g), static_cast<S *>(Rout));
     return cudaGetLastError();
 }
 
 template <typename real, typename S, int Q>
 cudaError_t ref_macro_t(const KParams &p, void *scratch, const void *RT_iso, const void *f, const void *g,
-                        cudaStream_t st)
+                        const void *Rin, cudaStream_t st)
 {
     const int B = 256;
     const dim3 G = node_grid(p.N, B);
     RefFields<real> w = ref_fields<real>(scratch, p.N, RT_iso);
-    k_moments<real, S, Q><<<G, B, 0, st>>>(p, static_cast<const S *>(f), static_cast<const S *>(g), w);
+    k_moments<real, S, Q><<<G, B, 0, st>>>(p, static_cast<const S *>(f), static_cast<const S *>(g),
+                                           static_cast<const S *>(Rin), w);
     k_stress<real, Q><<<G, B, 0, st>>>(p, w);
     k_macro<real, Q><<<G, B, 0, st>>>(p, w);
     return cudaGetLastError();
@@ -59,15 +60,16 @@ cudaError_t ref_macro_t(const KParams &p, void *scratch, const void *RT_iso, con
 
 template <typename real, typename S, int Q>
 cudaError_t ref_step_t(const KParams &p, void *scratch, const void *RT_iso, const void *f, const void *g, void *fo,
-                       void *go, cudaStream_t st)
+                       void *go, const void *Rin, void *Rout, cudaStream_t st)
 {
-    cudaError_t e = ref_macro_t<real, S, Q>(p, scratch, RT_iso, f, g, st);
+    cudaError_t e = ref_macro_t<real, S, Q>(p, scratch, RT_iso, f, g, Rin, st);
     if (e != cudaSuccess) return e;
     const int B = 256;
     RefFields<real> w = ref_fields<real>(scratch, p.N, RT_iso);
     k_collide<real, S, Q><<<node_grid(p.N, B), B, 0, st>>>(p, w, static_cast<const S *>(f),
                                                            static_cast<const S *>(g), static_cast<S *>(fo),
-                                                           static_cast<S *>(go));
+                                                           static_cast<S *>(go), static_cast<const S *>(Rin),
+                                                           static_cast<S *>(Rout));
     return cudaGetLastError();
 }
 
@@ -81,10 +83,11 @@ cudaError_t ref_export_t(const KParams &p, void *scratch, double R, float *rho, 
 }
 
 template <typename S, int Q>
-cudaError_t expand_t(const KParams &p, const void *src, double *dst, int which, cudaStream_t st)
+cudaError_t expand_t(const KParams &p, const void *src, const void *R, double *dst, int which, cudaStream_t st)
 {
     const int B = 256;
-    k_expand<S, Q><<<node_grid(p.N, B), B, 0, st>>>(p, static_cast<const S *>(src), dst, which);
+    k_expand<S, Q><<<node_grid(p.N, B), B, 0, st>>>(p, static_cast<const S *>(src), static_cast<const S *>(R), dst,
+                                                    which);
     return cudaGetLastError();
 }
 
