@@ -1,0 +1,77 @@
+"""Reduced-precision storage study (FP32, FP16, BF16 storage; FP32 arithmetic) against
+FP64: the 64^3 D3Q27 spinodal crop after 200 steps (pointwise density error against
+the CPU oracle), and droplet observables -- coexistence densities, Laplace pressure
+jump and spurious-current magnitude -- against the FP64 GPU path (bit-identical to
+the oracle).  Run with -s to see the table."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.eos as E
+import paper_2508_00577_gb300 as ev
+from paper_2508_00577_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+A, B = 0.1, 4.0
+PRECS = [(ev.LBM_FP32, "fp32"), (ev.LBM_FP16_DEV, "fp16"), (ev.LBM_BF16_DEV, "bf16")]
+
+
+def test_spinodal_crop_64cubed():
+    n, steps = 64, 200
+    _, Tc = E.critical_point(E.CS, A, B)
+    RT = 0.85 * Tc
+    s1, s2 = E.spinodal(E.CS, A, B, RT)
+    kappa = E.kappa_for_width(E.CS, A, B, RT, 4.0)
+    fields = inputs.spinodal_noise(n, n, n, 0.5 * (s1 + s2), RT, amplitude=0.01)
+    o = oracle.State(oracle.Params(Q=27, nx=n, ny=n, nz=n, eos=E.CS, a=A, b=B, kappa=kappa, tau=0.3), *fields)
+    o.step(steps)
+    ro = o.macro()[0]
+    errs = {}
+    for prec, name in PRECS:
+        p = ev.lbm_params.make(lattice=ev.LBM_D3Q27, nx=n, ny=n, nz=n, eos=ev.LBM_EOS_CS, a=A, b=B,
+                               kappa=kappa, precision=prec)
+        with ev.Lattice(p, *fields) as g:
+            g.step(steps)
+            errs[name] = float(np.max(np.abs(g.moments()[0] - ro) / ro))
+    print("\n64^3 D3Q27 spinodal crop, 200 steps, max |d rho|/rho vs FP64 oracle:", errs)
+    assert errs["fp32"] <= 1e-4
+    assert errs["fp16"] <= 1e-3
+    assert errs["bf16"] <= 2e-3
+
+
+def droplet_observables(rho, u, RT, nx, ny, R):
+    r = rho.reshape(ny, nx)
+    p = E.pressure(E.CS, A, B, RT, r)
+    inside = float(r[ny // 2 - 2:ny // 2 + 2, nx // 2 - 2:nx // 2 + 2].mean())
+    outside = float(r[:4, :4].mean())
+    dp = float(p[ny // 2 - 2:ny // 2 + 2, nx // 2 - 2:nx // 2 + 2].mean() - p[:4, :4].mean())
+    umax = float(np.abs(u).max())
+    return inside, outside, dp, umax
+
+
+def test_droplet_observables_by_precision():
+    nx = ny = 128
+    R, steps = 32.0, 3000
+    _, Tc = E.critical_point(E.CS, A, B)
+    RT = 0.8 * Tc
+    rv, rl = E.maxwell(E.CS, A, B, RT)
+    kappa = E.kappa_for_width(E.CS, A, B, RT, 4.0)
+    fields = inputs.droplet(nx, ny, R, rv, rl, RT)
+    res = {}
+    for prec, name in [(ev.LBM_FP64, "fp64")] + PRECS:
+        p = ev.lbm_params.make(nx=nx, ny=ny, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=kappa, precision=prec)
+        with ev.Lattice(p, *fields) as g:
+            g.step(steps)
+            rho, u, T, _ = g.moments()
+            res[name] = droplet_observables(rho, u, RT, nx, ny, R)
+    ref = res["fp64"]
+    print("\ndroplet R=32, T/Tc=0.8, 3000 steps: (rho_in, rho_out, dp, max|u|)")
+    for k, v in res.items():
+        rel = [abs(a - b) / abs(b) for a, b in zip(v, ref)]
+        print(f"  {k}: {v}  rel. diff vs fp64: {rel}")
+        if k == "fp64":
+            continue
+        assert rel[0] <= 1e-3 and rel[1] <= 1e-3
+        # dp is a small difference of large pressures: FP32/FP16 within 2 %, BF16 within 10 %.
+        assert rel[2] <= (0.1 if k == "bf16" else 2e-2)
