@@ -108,6 +108,15 @@ int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *T, double *F);
  * context's stream.  Errors: LBM_EINVAL, LBM_ECUDA. */
 int lbm_moments_device(lbm_ctx *ctx, float *d_rho, float *d_u, float *d_T);
 
+/* Restart from macroscopic fields held in DEVICE arrays (FP32): rho[N], u[D][N],
+ * T[N].  The populations become the local equilibria f^eq(rho, u, theta0) and
+ * (thermal) g^eq(rho, u, theta0, RT) of Eqs. f_eq and g_eq, exactly as lbm_init
+ * builds them, and the isothermal temperature field becomes R*T.  Contexts of
+ * precision FP32, FP16_DEV or BF16_DEV only (LBM_EINVAL for FP64); the fields
+ * are not checked for finiteness.  Asynchronous on the context's stream; the
+ * step count is kept.  Errors: LBM_EINVAL, LBM_ECUDA. */
+int lbm_reset_device(lbm_ctx *ctx, const float *d_rho, const float *d_u, const float *d_T);
+
 /* Copy the current post-collision populations to HOST arrays f[Q][N] and
  * g[Q][N] (g ignored and may be NULL when thermal = 0), converted to FP64
  * (deviation storage is expanded).  Synchronises the stream. */

@@ -1,0 +1,173 @@
+/* Learned surrogate for the Enskog-Vlasov lattice Boltzmann step: C ABI.
+ *
+ * A 4-level convolutional U-Net maps the macroscopic fields (rho, u_x, u_y, T)
+ * of 2-D periodic domains to their state one window of lattice Boltzmann steps
+ * later (it predicts the increment).  The lattice Boltzmann method of the paper
+ * (Sec. 3, Eqs. for the moments, the shifted equilibria and the relaxation,
+ * implemented in evlbm.h) generates its training data, is its fallback and
+ * judges its error; the paper itself has no learned component, so nothing in
+ * this header restates a passage of it beyond that.
+ *
+ * Arithmetic: BF16 weights and activations, FP32 accumulation on the tensor
+ * cores (tcgen05.mma kind::f16), FP32 master weights, gradients and Adam
+ * moments.  Activations are NHWC matrices [pixels][channels] with pixels
+ * ordered (sample, y, x), x fastest.
+ *
+ * Pointers named d_* are device pointers owned by the caller; host arrays are
+ * named h_* or documented as host.  All calls run on the stream given at
+ * creation (NULL = a stream the model creates) and are asynchronous unless
+ * they return a host value.  Errors: SUR_EINVAL for invalid sizes, layouts or
+ * NULL arguments (nothing is launched), SUR_ECUDA for a CUDA runtime error,
+ * SUR_ETIMEOUT when a tensor-core wait gave up (the result is then invalid;
+ * the context stays usable), SUR_ENOMEM for a failed allocation.
+ */
+#ifndef EVSUR_H
+#define EVSUR_H
+
+#include <stdint.h>
+
+#include "evlbm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { SUR_OK = 0, SUR_EINVAL = 1, SUR_ECUDA = 2, SUR_ENOMEM = 3, SUR_ETIMEOUT = 4 };
+
+/* ---------------------------------------------------------------------------
+ * Layer primitives (exposed for testing and for callers that build their own
+ * networks).  All matrices are BF16 unless stated.
+ * ------------------------------------------------------------------------- */
+
+/* Operand kinds of the tensor-core GEMM C[m][n] = sum_k A(m, k) B(n, k).
+ *
+ *  SUR_OP_DENSE   X(r, k) = p[r*ld + c0 + k]                      (row-major)
+ *  SUR_OP_CONV3   X(r, k) = p[nb(r, tap)*ld + c0 + c]  with k = tap*C + c,
+ *                 tap = (dy+1)*3 + (dx+1), nb(r, tap) the periodic neighbour
+ *                 (y+dy, x+dx) of pixel r on an H x W grid; k >= 9C reads 0.
+ *                 (Implicit im2col of a 3x3 periodic convolution.)
+ *  SUR_OP_UPADJ   X(r, k) = p[fine(r, s)*ld + c0 + c]  with k = s*C + c, r a
+ *                 pixel of the coarse H x W grid and fine(r, s) its child
+ *                 (2y + s/2, 2x + s%2) on the 2H x 2W grid; k >= 4C reads 0.
+ *  SUR_OP_TDENSE  X(r, k) = p[k*ld + c0 + r]                      (transposed)
+ *  SUR_OP_TCONV3  X(r, k) = p[nb(k, tap)*ld + c0 + c]  with r = tap*C + c
+ *  SUR_OP_TUP     X(r, k) = p[fine(k, s)*ld + c0 + c]  with r = s*C + c
+ *
+ * Rows r >= rows and K indices k >= K read zero.  C, H and W are powers of
+ * two, C >= 8; ld and c0 are multiples of 8 elements and p is 16-byte aligned.
+ * Memory is read in 8-element chunks: a DENSE operand needs c0 + K rounded up
+ * to 8 <= ld, a TDENSE operand c0 + rows rounded up to 8 <= ld, and a gather
+ * kind c0 + C <= ld (SUR_EINVAL otherwise). */
+enum { SUR_OP_DENSE = 0, SUR_OP_CONV3 = 1, SUR_OP_UPADJ = 2, SUR_OP_TDENSE = 3, SUR_OP_TCONV3 = 4, SUR_OP_TUP = 5 };
+
+typedef struct sur_operand {
+    const void *p; /* device, BF16 */
+    int kind;      /* SUR_OP_* */
+    int ld, c0;    /* row stride and first column, elements */
+    int C;         /* channels of the gathered tensor (gather kinds) */
+    int rows;      /* valid rows of the operand */
+    int H, W;      /* pixel grid of the gather kinds (coarse grid for UPADJ/TUP) */
+} sur_operand;
+
+/* Epilogues.  acc is the FP32 accumulator of C[m][n]; bias (FP32, may be NULL
+ * except for SUR_EPI_CONV and SUR_EPI_SHUF) is indexed by n (by n % cout for SHUF).
+ *  SUR_EPI_BF16        out[m*ldo + co0 + n] = bf16(acc + bias)
+ *  SUR_EPI_F32         out[m*ldo + co0 + n] = acc + bias           (FP32 out)
+ *  SUR_EPI_F32_ATOMIC  out[m*ldo + co0 + n] += acc                 (FP32 out, split-K)
+ *  SUR_EPI_CONV        z = acc + bias; out[...] = bf16(z) (skipped when out is NULL),
+ *                      y[m*ldy + cy0 + n] = bf16(silu(z)),  silu(z) = z / (1 + e^-z)
+ *  SUR_EPI_SHUF        2x2 stride-2 transposed convolution: n = s*cout + c,
+ *                      y[fine(m, s)*ldy + cy0 + c] = bf16(acc + bias[c]) on the
+ *                      2H x 2W grid of the coarse grid (shuf_H, shuf_W) of m. */
+enum { SUR_EPI_BF16 = 0, SUR_EPI_F32 = 1, SUR_EPI_F32_ATOMIC = 2, SUR_EPI_CONV = 3, SUR_EPI_SHUF = 4 };
+
+typedef struct sur_gemm_args {
+    sur_operand a, b;
+    int M, N, K;       /* output rows (any >= 1), columns (multiple of 32), reduction length (>= 1) */
+    int splits;        /* K split across CTAs (>= 1; > 1 only with SUR_EPI_F32_ATOMIC) */
+    int epi;           /* SUR_EPI_* */
+    const float *bias;
+    void *out;         /* BF16 or FP32 per epi */
+    int ldo, co0;
+    void *y;           /* BF16, SUR_EPI_CONV / SUR_EPI_SHUF */
+    int ldy, cy0;
+    int shuf_cout, shuf_H, shuf_W;
+} sur_gemm_args;
+
+/* One GEMM on the tensor cores (128 x {32,64,128} CTA tiles, 64-deep K blocks,
+ * 3-4 stage cp.async pipeline, one thread issuing tcgen05.mma into a TMEM
+ * accumulator).  d_status (device int) is set to 1 if a wait gave up. */
+int sur_gemm(const sur_gemm_args *g, int *d_status, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * The model.
+ * ------------------------------------------------------------------------- */
+typedef struct sur_model sur_model;
+
+/* Architecture (fixed): input 4 channels zero-padded to 8; levels of widths
+ * base, 2 base, 4 base, 8 base (base = 32); two 3x3 periodic convolutions with
+ * bias and SiLU per level; 2x2 average pooling down; 2x2 stride-2 transposed
+ * convolutions with bias up, concatenated after the skip tensor; a 1x1 head to
+ * 4 channels.  H and W are powers of two >= 16.
+ *
+ * Parameters (FP32, canonical order, packed without gaps):
+ *   14 convolutions in execution order c00 c01 c10 c11 c20 c21 c30 c31 c22 c23
+ *   c12 c13 c02 c03, each W [Kp][Cout] with row tap*Cin + ci (Kp = 9 Cin rounded
+ *   up to a multiple of 64, rows >= 9 Cin zero) followed by bias [Cout];
+ *   3 transposed convolutions u2 u1 u0, each W [4 Cout][Cin] with row s*Cout + co,
+ *   s = 2 di + dj the child offset, followed by bias [Cout];
+ *   the head W [4][base] and bias [4].
+ * Initialised with uniform(-sqrt(6/fan_in), sqrt(6/fan_in)) weights from a
+ * splitmix64 stream of seed, zero biases, and zero weights on padded inputs. */
+int sur_init(int H, int W, int base_ch, uint64_t seed, void *stream, sur_model **out);
+int sur_free(sur_model *m);                                      /* NULL-safe */
+long long sur_num_params(const sur_model *m);
+int sur_get_params(sur_model *m, float *h_params, long long n);  /* synchronises */
+int sur_set_params(sur_model *m, const float *h_params, long long n);
+int sur_get_grads(sur_model *m, float *h_grads, long long n);    /* gradients of the last forward_backward */
+
+/* Normalisation: the network sees (x_c - in_mean[c]) / in_scale[c] and its
+ * output o_c means an increment out_scale[c] * o_c of field c (host arrays of 4). */
+int sur_set_norm(sur_model *m, const float *in_mean, const float *in_scale, const float *out_scale);
+
+/* Fields are FP32 planar device arrays [4][batch*H*W]: rho, u_x, u_y, T.
+ * forward_backward: loss = mean over pixels and channels of
+ * (o - (y - x)/out_scale)^2; gradients of it (overwritten) into the model.
+ * train_step: forward_backward then one Adam step (lr, beta1 0.9, beta2 0.999,
+ * eps 1e-8, bias-corrected).  loss (host, may be NULL) synchronises. */
+int sur_forward_backward(sur_model *m, const float *d_x, const float *d_y, int batch, float *loss);
+int sur_train_step(sur_model *m, const float *d_x, const float *d_y, int batch, float lr, float *loss);
+/* d_y = x + out_scale * o (d_y may equal d_x). */
+int sur_infer(sur_model *m, const float *d_x, float *d_y, int batch);
+
+/* Per-domain indicators (FP64 sums over each H x W domain of a planar field
+ * array): d_out[2 b] = sum rho, d_out[2 b + 1] = number of nodes with
+ * rho > rho_mid. */
+int sur_indicators(const float *d_fields, int batch, int H, int W, float rho_mid, double *d_out, void *stream);
+
+/* Rollout of `windows` windows of `steps` lattice steps each on the fields
+ * d_fields (in/out).  Each window the surrogate proposes the next state; if for
+ * any domain the mass differs from the mass at the start of the rollout by more
+ * than max_mass_drift (relative), the liquid node count (rho > rho_mid) differs
+ * from that of the previous window by more than max_area_change (relative), or
+ * a field is not finite, the proposal is discarded and the window is advanced
+ * by the lattice Boltzmann context lb instead (nz = batch layers of H x W,
+ * D2Q9, not FP64), restarted from the local equilibrium of the current fields
+ * (lbm_reset_device).
+ * h_used_lb (host, windows entries, may be NULL) records 1 for such windows;
+ * *n_fallback (host) counts them.  Synchronises once per window. */
+typedef struct sur_rollout_cfg {
+    int windows, steps;
+    float rho_mid, max_mass_drift, max_area_change;
+} sur_rollout_cfg;
+int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur_rollout_cfg *cfg,
+                unsigned char *h_used_lb, int *n_fallback);
+
+/* Description of the last error of this model (static string storage). */
+const char *sur_last_error(const sur_model *m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

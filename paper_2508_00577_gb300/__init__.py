@@ -18,7 +18,8 @@ __all__ = [
     "lbm_params", "lib", "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_device",
     "lbm_populations", "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_set_tile",
     "lbm_get_tile", "lbm_autotune", "lbm_sync", "lbm_free",
-    "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "lbm_step_noalloc", "LBMError", "Lattice",
+    "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "lbm_step_noalloc", "lbm_reset_device",
+    "LBMError", "Lattice",
     "LBM_D2Q9", "LBM_D3Q27", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
     "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS", "Batch",
 ]
@@ -38,7 +39,7 @@ EXPORTED_SYMBOLS = (
     "lbm_autotune", "lbm_sync", "lbm_free", "lbm_last_error", "lbm_coexistence", "lbm_critical_point",
     "lbm_step_noalloc", "lbm_batch_init", "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_tile",
     "lbm_batch_get_tile", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_batch_nodes",
-    "lbm_batch_free", "lbm_batch_last_error",
+    "lbm_batch_free", "lbm_batch_last_error", "lbm_reset_device",
 )
 
 
@@ -95,6 +96,7 @@ def lib():
             L.lbm_step.argtypes = [vp, ctypes.c_int]
             L.lbm_moments.argtypes = [vp, dp, dp, dp, dp]
             L.lbm_moments_device.argtypes = [vp, vp, vp, vp]
+            L.lbm_reset_device.argtypes = [vp, vp, vp, vp]
             L.lbm_populations.argtypes = [vp, dp, dp]
             L.lbm_conserved.argtypes = [vp, dp]
             L.lbm_step_count.argtypes = [vp]
@@ -185,6 +187,11 @@ def lbm_moments_device(ctx, d_rho=0, d_u=0, d_T=0):
     """Device pointers (ints, e.g. tensor.data_ptr()) of FP32 outputs; 0 = skip."""
     _check(lib().lbm_moments_device(ctx, ctypes.c_void_p(d_rho or None), ctypes.c_void_p(d_u or None),
                                     ctypes.c_void_p(d_T or None)), ctx)
+
+
+def lbm_reset_device(ctx, d_rho, d_u, d_T):
+    """Populations := local equilibria of device FP32 fields (int device pointers)."""
+    _check(lib().lbm_reset_device(ctx, d_rho, d_u, d_T), ctx)
 
 
 def lbm_populations(ctx, f, g=None):

@@ -43,7 +43,7 @@ def _stale(out: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(HERE, "..", "include", "evlbm.h"))
+    headers += [os.path.join(HERE, "..", "include", h) for h in ("evlbm.h", "evsur.h")]
     objs, jobs = [], []
     for src in sources():
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))

@@ -150,6 +150,15 @@ void free_all(lbm_ctx *c)
 
 }  // namespace
 
+namespace {
+// RT = R * T on the device (FP32 contexts keep their scratch fields in FP32).
+__global__ void k_scale_field(const float *T, float R, long long N, float *RT)
+{
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x)
+        RT[n] = R * T[n];
+}
+}  // namespace
+
 extern "C" {
 
 int lbm_init(const lbm_params *params, const double *rho, const double *u, const double *T, void *stream,
@@ -284,6 +293,23 @@ int lbm_moments(lbm_ctx *c, double *rho, double *u, double *T, double *F)
     if (u && (rc = copy_field(c, O::u, c->D * N, u, 1.0))) return rc;
     if (T && (rc = copy_field(c, O::RT, N, T, c->P.R))) return rc;
     if (F && (rc = copy_field(c, O::F, c->D * N, F, 1.0))) return rc;
+    return LBM_OK;
+}
+
+int lbm_reset_device(lbm_ctx *c, const float *d_rho, const float *d_u, const float *d_T)
+{
+    if (!c) return LBM_EINVAL;
+    if (fp64(c)) return fail(c, LBM_EINVAL, "lbm_reset_device needs an FP32, FP16_DEV or BF16_DEV context");
+    if (!d_rho || !d_u || !d_T) return fail(c, LBM_EINVAL, "d_rho, d_u and d_T must be device arrays");
+    const long long N = c->N;
+    long long blocks = (N + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_scale_field<<<(int)blocks, 256, 0, c->stream>>>(d_T, float(c->P.R), N, static_cast<float *>(c->RT_iso));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = evlbm::ref_init_f32(c->P.precision, c->Q, c->K, d_rho, d_u, c->RT_iso, c->f[c->cur], c->g[c->cur],
+                                c->R[c->cur], c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_reset_device");
     return LBM_OK;
 }
 

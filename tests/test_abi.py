@@ -12,6 +12,7 @@ import paper_2508_00577_gb300 as ev
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "evlbm.h")
+SUR_HEADER = os.path.join(ROOT, "include", "evsur.h")
 
 
 def declared_symbols():
@@ -21,6 +22,37 @@ def declared_symbols():
 
 def test_header_declares_the_binding_names():
     assert declared_symbols() == sorted(ev.EXPORTED_SYMBOLS)
+
+
+def test_surrogate_header_declares_the_binding_names():
+    from paper_2508_00577_gb300 import surrogate as S
+    text = open(SUR_HEADER).read()
+    names = sorted(set(re.findall(r"^(?:int|long long|const char \*)\s*(sur_\w+)\s*\(", text, re.M)))
+    assert names == sorted(S.EXPORTED_SYMBOLS)
+    L = S.lib()
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_surrogate_structs_match_header():
+    """Field order of sur_operand, sur_gemm_args and sur_rollout_cfg as in the header."""
+    from paper_2508_00577_gb300 import surrogate as S
+    text = open(SUR_HEADER).read()
+    for cname, cls in (("sur_operand", S.sur_operand), ("sur_gemm_args", S.sur_gemm_args),
+                       ("sur_rollout_cfg", S.sur_rollout_cfg)):
+        body = text[text.index(f"typedef struct {cname} {{"):text.index(f"}} {cname};")]
+        body = body[body.index("{") + 1:]
+        flat = []
+        for decl in re.findall(r"^\s*(?:const\s+)?(?:int|float|void|sur_operand)\s*\**\s*([\w, *]+);", body, re.M):
+            flat += [n.strip().lstrip("*") for n in decl.split(",")]
+        assert [f[0] for f in cls._fields_] == flat, cname
+
+
+def test_surrogate_layout_matches_oracle():
+    from paper_2508_00577_gb300 import surrogate as S
+    import oracle.unet as U
+    layout, n = S.param_layout()
+    assert n == U.unpack(np.zeros(n))["_n"]
 
 
 def test_library_exports_every_declared_symbol():
