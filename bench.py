@@ -331,6 +331,163 @@ def run_ensemble(args):
     return 0
 
 
+# Surrogate workload (A12): droplet-pair domains of 256^2 drawn like the ensemble's
+# (radii U[8, 48], gap U[2, 10], T/Tc U[0.7, 0.9]); kappa = 0.2 (10-90 % width 5.3 at
+# T/Tc = 0.7, 9.6 at 0.9) because at kappa = 0.116 about 5 % of these domains diverge
+# before 5000 steps; windows of 50 steps.
+SUR_N, SUR_KAPPA, SUR_STEPS, SUR_WINDOWS = 256, 0.2, 50, 100
+
+
+def surrogate_fields(ev, doms, Tc):
+    from paper_2508_00577_gb300 import inputs
+    cache, rho, T = {}, [], []
+    for dm in doms:
+        tr = round(dm["tr"], 4)
+        if tr not in cache:
+            cache[tr] = ev.lbm_coexistence(1, A, B, tr * Tc)
+        rv, rl = cache[tr]
+        r, _, t = inputs.two_droplets(SUR_N, SUR_N, dm["r1"], dm["r2"], dm["gap"], rv, rl, dm["tr"] * Tc)
+        rho.append(r)
+        T.append(t)
+    rho, T = np.concatenate(rho), np.concatenate(T)
+    return rho, np.zeros((2, rho.size)), T
+
+
+def run_surrogate(args):
+    """Train the U-Net surrogate on lattice Boltzmann trajectories, then compare the
+    time to solution of a 5000-step rollout (surrogate windows with lattice Boltzmann
+    fallback) with the plain FP32 lattice Boltzmann run on held-out domains."""
+    import torch
+
+    import paper_2508_00577_gb300 as ev
+    from paper_2508_00577_gb300 import inputs
+    from paper_2508_00577_gb300 import surrogate as S
+
+    dev = "cuda"
+    _, Tc = ev.lbm_critical_point(1, A, B)
+    Mb = SUR_N * SUR_N
+
+    def params(nd):
+        return ev.lbm_params.make(nx=SUR_N, ny=SUR_N, nz=nd, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=SUR_KAPPA, tau=TAU,
+                                  precision=ev.LBM_FP32)
+
+    def trajectories(doms):
+        nd = len(doms)
+        N = nd * Mb
+        snaps = torch.empty((SUR_WINDOWS + 1, 4, N), device=dev)
+        with ev.Lattice(params(nd), *surrogate_fields(ev, doms, Tc)) as g:
+            for w in range(SUR_WINDOWS + 1):
+                if w:
+                    g.step(SUR_STEPS)
+                base = snaps.data_ptr() + w * 16 * N
+                ev.lbm_moments_device(g.ctx, base, base + 4 * N, base + 12 * N)
+            ev.lbm_sync(g.ctx)
+        torch.cuda.synchronize()
+        return snaps
+
+    train_doms = inputs.ensemble_domains(args.train_domains, seed=1, side_min=SUR_N, side_max=SUR_N)
+    test_doms = inputs.ensemble_domains(args.domains, seed=2, side_min=SUR_N, side_max=SUR_N)
+    t0 = time.perf_counter()
+    snaps = trajectories(train_doms)
+    t_data = time.perf_counter() - t0
+    x, y = snaps[:-1], snaps[1:]
+    mean = x.mean(dim=(0, 2)).cpu().numpy()
+    scale = np.maximum(x.std(dim=(0, 2)).cpu().numpy(), 1e-6)
+    oscale = np.maximum((y - x).std(dim=(0, 2)).cpu().numpy(), 1e-9)
+    view = snaps.reshape(SUR_WINDOWS + 1, 4, len(train_doms), Mb)
+    bs = args.batch
+    rng = np.random.default_rng(0)
+    model = S.Surrogate(SUR_N, SUR_N, seed=3)
+    model.set_norm(mean, scale, oscale)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = []
+    for it in range(args.train_steps):
+        w = torch.as_tensor(rng.integers(0, SUR_WINDOWS, bs), device=dev)
+        d = torch.as_tensor(rng.integers(0, len(train_doms), bs), device=dev)
+        xb = view[w, :, d, :].permute(1, 0, 2).reshape(4, bs * Mb).contiguous()
+        yb = view[w + 1, :, d, :].permute(1, 0, 2).reshape(4, bs * Mb).contiguous()
+        torch.cuda.synchronize()
+        lr = args.lr * 0.5 * (1 + np.cos(np.pi * it / args.train_steps)) + 1e-6
+        want = it % 200 == 0 or it == args.train_steps - 1
+        loss = model.train_step(xb.data_ptr(), yb.data_ptr(), bs, float(lr), want_loss=want)
+        if want:
+            losses.append((it, round(loss, 5)))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del snaps, view, x, y
+
+    # Held-out domains: the plain lattice Boltzmann run is the reference and the judge.
+    nd = len(test_doms)
+    N = nd * Mb
+    rho0, u0, T0 = surrogate_fields(ev, test_doms, Tc)
+    steps = SUR_STEPS * SUR_WINDOWS
+    ref = torch.empty((4, N), device=dev)
+    with ev.Lattice(params(nd), rho0, u0, T0) as g:
+        tile = ev.lbm_autotune(g.ctx, 2)
+        g.step(args.warmup)
+        torch.cuda.synchronize()
+    with ev.Lattice(params(nd), rho0, u0, T0) as g:
+        ev.lbm_set_tile(g.ctx, *tile)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(steps)
+        ev.lbm_moments_device(g.ctx, ref.data_ptr(), ref.data_ptr() + 4 * N, ref.data_ptr() + 12 * N)
+        ev.lbm_sync(g.ctx)
+        torch.cuda.synchronize()
+        t_lb = time.perf_counter() - t0
+    start = torch.tensor(np.stack([rho0, u0[0], u0[1], T0]), dtype=torch.float32, device=dev).contiguous()
+    rho_mid = float(0.5 * (start[0].max() + start[0].min()))
+
+    def rel_err(a):
+        per = [float((a[0, k * Mb:(k + 1) * Mb] - ref[0, k * Mb:(k + 1) * Mb]).norm()
+                     / ref[0, k * Mb:(k + 1) * Mb].norm()) for k in range(nd)]
+        return float((a[0] - ref[0]).norm() / ref[0].norm()), max(per)
+
+    results = {}
+    for name, thr in (("fallback", (args.max_mass_drift, args.max_area_change)), ("surrogate_only", (1e30, 1e30))):
+        with ev.Lattice(params(nd), rho0, u0, T0) as lb:
+            ev.lbm_set_tile(lb.ctx, *tile)
+            d = start.clone()
+            model.infer(d.data_ptr(), torch.empty_like(d).data_ptr(), nd)   # warm the arena
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nfb, used = model.rollout(lb.ctx, d.data_ptr(), nd, SUR_WINDOWS, SUR_STEPS, rho_mid, thr[0], thr[1])
+            torch.cuda.synchronize()
+            t_roll = time.perf_counter() - t0
+        err, worst = rel_err(d)
+        results[name] = {"seconds": t_roll, "speedup_vs_lb": t_lb / t_roll, "fallback_windows": int(nfb),
+                         "rho_rel_l2": err, "rho_rel_l2_worst_domain": worst}
+    # Inference throughput alone.
+    o = torch.empty_like(start)
+    for _ in range(3):
+        model.infer(start.data_ptr(), o.data_ptr(), nd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        model.infer(start.data_ptr(), o.data_ptr(), nd)
+    torch.cuda.synchronize()
+    t_inf = (time.perf_counter() - t0) / 10
+    flops = 17.93e9 * nd
+    model.close()
+    fb = results["fallback"]
+    print(json.dumps({
+        "metric": "surrogate+fallback time-to-solution speedup vs plain FP32 LB", "value": fb["speedup_vs_lb"],
+        "unit": "x", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+        "meets_rho_rel_l2_1e-2": fb["rho_rel_l2"] <= 1e-2,
+        "config": {"workload": f"{nd} held-out droplet-pair domains of {SUR_N}^2, {steps} steps = {SUR_WINDOWS} windows "
+                               f"of {SUR_STEPS}; trained on {len(train_doms)} domains x {SUR_WINDOWS} windows",
+                   "kappa": SUR_KAPPA, "tau": TAU, "train_steps": args.train_steps, "batch": bs,
+                   "thresholds": {"max_mass_drift": args.max_mass_drift, "max_area_change": args.max_area_change}},
+        "plain_lb_seconds": t_lb, "plain_lb_mlups": N * steps / t_lb / 1e6,
+        "rollouts": results,
+        "inference": {"ms_per_window": t_inf * 1e3, "tflops": flops / t_inf / 1e12, "batch": nd},
+        "training": {"seconds": t_train, "ms_per_step": t_train / args.train_steps * 1e3, "data_seconds": t_data,
+                     "loss": losses},
+    }), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,14 +498,25 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed launch shape W,H of the fused kernel")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble"],
-                    help="sweep: the headline droplet Laplace sweep; ensemble: 512 uneven domains")
-    ap.add_argument("--domains", type=int, default=512)
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate"],
+                    help="sweep: the headline droplet Laplace sweep; ensemble: 512 uneven domains; "
+                         "surrogate: U-Net surrogate with lattice Boltzmann fallback vs plain LB")
+    ap.add_argument("--domains", type=int, default=None, help="ensemble: 512; surrogate: 32 held-out domains")
+    ap.add_argument("--train-domains", type=int, default=64)
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--max-mass-drift", type=float, default=1e-3)
+    ap.add_argument("--max-area-change", type=float, default=0.02)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "ensemble":
+        args.domains = args.domains or 512
         return run_ensemble(args)
+    if args.workload == "surrogate":
+        args.domains = args.domains or 32
+        return run_surrogate(args)
     return run(args)
 
 

@@ -152,8 +152,11 @@ int sur_indicators(const float *d_fields, int batch, int H, int W, float rho_mid
  * from that of the previous window by more than max_area_change (relative), or
  * a field is not finite, the proposal is discarded and the window is advanced
  * by the lattice Boltzmann context lb instead (nz = batch layers of H x W,
- * D2Q9, not FP64), restarted from the local equilibrium of the current fields
- * (lbm_reset_device).
+ * D2Q9, not FP64).  The first fallback window and every fallback window that
+ * follows an accepted surrogate window restart lb from the local equilibrium of
+ * the current fields (lbm_reset_device); consecutive fallback windows continue
+ * the lattice Boltzmann state, so a rollout in which every window falls back is
+ * exactly a plain lattice Boltzmann run from the equilibrium of the start fields.
  * h_used_lb (host, windows entries, may be NULL) records 1 for such windows;
  * *n_fallback (host) counts them.  Synchronises once per window. */
 typedef struct sur_rollout_cfg {

@@ -692,6 +692,10 @@ int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur
     if ((rc = check_status(m, nullptr))) return rc;
     for (int b = 0; b < batch; ++b) mass0[b] = cur[2 * b];
     int fallbacks = 0;
+    // lb_current: the context's populations are the lattice Boltzmann state of
+    // d_fields (true after a fallback window), so the next fallback window
+    // continues from them instead of restarting from the local equilibrium.
+    bool lb_current = false;
     for (int w = 0; w < cfg->windows; ++w) {
         if ((rc = forward(m, d_fields, batch, false))) return rc;
         CK(evsur::head(m->Y03, N, m->P + m->head_w, m->P + m->head_b, m->norm, d_fields, nullptr, 1, nullptr,
@@ -711,10 +715,12 @@ int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur
         if (accept) {
             CK(cudaMemcpyAsync(d_fields, m->next, sizeof(float) * 4 * N, cudaMemcpyDeviceToDevice, m->stream));
             cur.swap(nxt);
+            lb_current = false;
         } else {
-            // Lattice Boltzmann window from the local equilibrium of the current fields.
+            // Lattice Boltzmann window; after a surrogate window it restarts from the
+            // local equilibrium of the current fields.
             CK(cudaStreamSynchronize(m->stream));
-            int lrc = lbm_reset_device(lb, d_fields, d_fields + N, d_fields + 3 * N);
+            int lrc = lb_current ? LBM_OK : lbm_reset_device(lb, d_fields, d_fields + N, d_fields + 3 * N);
             if (lrc == LBM_OK) lrc = lbm_step(lb, cfg->steps);
             if (lrc == LBM_OK) lrc = lbm_moments_device(lb, d_fields, d_fields + N, d_fields + 3 * N);
             if (lrc == LBM_OK) lrc = lbm_sync(lb);
@@ -722,6 +728,7 @@ int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur
             CK(evsur::indicators(d_fields, batch, Mb, cfg->rho_mid, m->ind, m->status + 1, m->stream));
             CK(cudaMemcpyAsync(cur.data(), m->ind, sizeof(double) * 2 * batch, cudaMemcpyDeviceToHost, m->stream));
             if ((rc = check_status(m, nullptr))) return rc;
+            lb_current = true;
             ++fallbacks;
         }
         if (h_used_lb) h_used_lb[w] = accept ? 0 : 1;

@@ -54,17 +54,6 @@ struct Op {
     int lc, lh, lw;   // log2 C, log2 H, log2 W
 };
 
-// Periodic neighbour of pixel q at tap = (dy+1)*3 + (dx+1) on a 2^lh x 2^lw grid.
-__device__ __forceinline__ long long nb_pixel(long long q, int tap, int lh, int lw)
-{
-    const int W = 1 << lw, H = 1 << lh;
-    const int x = (int)(q & (W - 1)), y = (int)((q >> lw) & (H - 1));
-    const long long b = q >> (lw + lh);
-    const int ty = (tap * 11) >> 5;   // tap / 3 for tap in [0, 8]
-    const int ys = (y + ty - 1) & (H - 1), xs = (x + tap - 3 * ty - 1) & (W - 1);
-    return (((b << lh) | ys) << lw) | xs;
-}
-
 // Child s = 2 di + dj of coarse pixel q (grid 2^lh x 2^lw) on the 2x finer grid.
 __device__ __forceinline__ long long fine_pixel(long long q, int s, int lh, int lw)
 {
@@ -74,63 +63,138 @@ __device__ __forceinline__ long long fine_pixel(long long q, int s, int lh, int 
     return (((b << (lh + 1)) | (2 * y + (s >> 1))) << (lw + 1)) | (2 * x + (s & 1));
 }
 
-// Fill one operand tile of ROWS x 64 (K) in shared memory for the K block that
-// starts at kbase (K indices >= kend read zero).
+// Per-thread loader state of one operand.  Producer thread t (0..127) owns
+// ROWS/16 16-byte chunks of every stage:
+//   K-major operands (DENSE, CONV3, UPADJ): rows r_i = (t >> 3) + 16 i, K group t & 7;
+//     the rows (pixels) are fixed for the whole K loop, so their coordinates are
+//     computed once; a stage only changes the tap.
+//   MN-major operands (TDENSE, TCONV3, TUP): row group g = t % (ROWS/8) (fixed: one
+//     tap and 8 channels), K indices (pixels) k_j = t / (ROWS/8) + (1024/ROWS) j.
+template <int ROWS> struct Loader {
+    static constexpr int NCH = ROWS / 16;   // chunks per thread per stage
+    int x[NCH], yb[NCH];                     // K-major gathers: pixel x and (sample*H + y)
+    bool rv[NCH];                            // K-major: row valid
+    long long rowoff[NCH];                   // K-major dense: row offset in elements
+    int g, c, dy, dx;                        // MN-major: row group, channel, tap offsets
+    bool gv;
+};
+
+template <int ROWS>
+__device__ __forceinline__ void loader_init(const Op &o, Loader<ROWS> &L, long long row0, int t)
+{
+    if (o.kind <= SUR_OP_UPADJ) {
+#pragma unroll
+        for (int i = 0; i < Loader<ROWS>::NCH; ++i) {
+            const long long q = row0 + (t >> 3) + 16 * i;
+            L.rv[i] = q < o.rows;
+            L.rowoff[i] = q * o.ld + o.c0;
+            L.x[i] = (int)(q & ((1 << o.lw) - 1));
+            L.yb[i] = (int)(q >> o.lw);
+        }
+    } else {
+        constexpr int G = ROWS / 8;
+        L.g = t % G;
+        const long long r0 = row0 + 8 * L.g;
+        L.gv = r0 < o.rows;
+        L.c = (int)r0;
+        L.dy = L.dx = 0;
+        if (o.kind != SUR_OP_TDENSE) {
+            const int tap = (int)(r0 >> o.lc);
+            L.c = (int)(r0 & ((1 << o.lc) - 1));
+            L.gv = L.gv && tap < (o.kind == SUR_OP_TCONV3 ? 9 : 4);
+            if (o.kind == SUR_OP_TCONV3) {
+                L.dy = ((tap * 11) >> 5) - 1;
+                L.dx = tap - 3 * (L.dy + 1) - 1;
+            } else {
+                L.dy = tap >> 1;   // child offsets di, dj
+                L.dx = tap & 1;
+            }
+        }
+    }
+}
+
+// Pixel at offset (dy, dx) from (x, yb = sample*H + y), periodic on a 2^lh x 2^lw grid.
+__device__ __forceinline__ long long shifted(int x, int yb, int dy, int dx, int lh, int lw)
+{
+    const int hm = (1 << lh) - 1, wm = (1 << lw) - 1;
+    const int ys = (yb & ~hm) | ((yb + dy) & hm);
+    return ((long long)ys << lw) | ((x + dx) & wm);
+}
+
+// Child (di, dj) on the 2x finer grid of coarse pixel (x, yb).
+__device__ __forceinline__ long long child(int x, int yb, int di, int dj, int lw)
+{
+    return ((long long)(2 * yb + di) << (lw + 1)) | (2 * x + dj);
+}
+
+// Fill one operand tile of ROWS x 64 (K) for the K block starting at kbase
+// (K indices >= kend read zero).
 //   K-major tile: core matrix (row group r/8, k group k/8) at ((r/8)*8 + k/8)*128 B,
 //                 row r%8 at +16 B (LBO = 128, SBO = 1024).
 //   MN-major tile: core matrix (k group k/8, row group g) at ((k/8)*(ROWS/8) + g)*128 B,
 //                 k%8 at +16 B (SBO = 128, LBO = ROWS*16).
 template <int ROWS>
-__device__ __forceinline__ void load_tile(const Op &o, uint32_t s, long long row0, long long kbase, long long kend,
-                                          int t)
+__device__ __forceinline__ void load_tile(const Op &o, const Loader<ROWS> &L, uint32_t s, long long kbase,
+                                          long long kend, int t)
 {
+    constexpr int NCH = Loader<ROWS>::NCH;
     if (o.kind <= SUR_OP_UPADJ) {
         const int k8 = t & 7;
         const long long k = kbase + k8 * 8;
         bool kval = k < kend;
-        int tap = 0, cc = (int)k;
+        int tap = 0, cc = 0;
         if (o.kind != SUR_OP_DENSE) {
-            const long long q = k >> 3;
-            tap = (int)(q >> (o.lc - 3));
-            cc = (int)(q & ((1 << (o.lc - 3)) - 1)) << 3;
+            const int q = (int)(k >> 3);
+            tap = q >> (o.lc - 3);
+            cc = (q & ((1 << (o.lc - 3)) - 1)) << 3;
             kval = kval && tap < (o.kind == SUR_OP_CONV3 ? 9 : 4);
         }
-#pragma unroll 4
-        for (int r = t >> 3; r < ROWS; r += 16) {
-            const long long row = row0 + r;
-            const bool v = kval && row < o.rows;
+        int dy, dx;
+        if (o.kind == SUR_OP_CONV3) {
+            dy = ((tap * 11) >> 5) - 1;
+            dx = tap - 3 * (dy + 1) - 1;
+        } else {
+            dy = tap >> 1;
+            dx = tap & 1;
+        }
+        const uint32_t sk = s + (uint32_t)(k8 * 128 + ((t >> 3) & 7) * 16 + ((t >> 6) << 10));
+#pragma unroll
+        for (int i = 0; i < NCH; ++i) {
+            const bool v = kval && L.rv[i];
             const bf16 *src = o.p;
             if (v) {
-                long long pix = row;
-                if (o.kind == SUR_OP_CONV3) pix = nb_pixel(row, tap, o.lh, o.lw);
-                else if (o.kind == SUR_OP_UPADJ) pix = fine_pixel(row, tap, o.lh, o.lw);
-                src = o.p + pix * o.ld + o.c0 + cc;
+                if (o.kind == SUR_OP_DENSE) {
+                    src = o.p + L.rowoff[i] + k;
+                } else {
+                    const long long pix = o.kind == SUR_OP_CONV3 ? shifted(L.x[i], L.yb[i], dy, dx, o.lh, o.lw)
+                                                                 : child(L.x[i], L.yb[i], dy, dx, o.lw);
+                    src = o.p + pix * o.ld + o.c0 + cc;
+                }
             }
-            cp_async16(s + (uint32_t)((((r >> 3) << 3) + k8) * 128 + (r & 7) * 16), src, v);
+            // row r = (t >> 3) + 16 i: group r/8 = (t >> 6) + 2 i, r % 8 = (t >> 3) & 7
+            cp_async16(sk + (uint32_t)(i * 2048), src, v);
         }
     } else {
         constexpr int G = ROWS / 8;
-        const int g = t % G;
-        const long long r0 = row0 + 8 * g;
-        int tap = 0, c = (int)r0;
-        bool gval = r0 < o.rows;
-        if (o.kind != SUR_OP_TDENSE) {
-            tap = (int)(r0 >> o.lc);
-            c = (int)(r0 & ((1 << o.lc) - 1));
-            gval = gval && tap < (o.kind == SUR_OP_TCONV3 ? 9 : 4);
-        }
-#pragma unroll 4
-        for (int k = t / G; k < BK; k += 128 / G) {
+        constexpr int KSTEP = 128 / G;
+        const int hm = (1 << o.lh) - 1;
+        (void)hm;
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            const int k = t / G + KSTEP * j;
             const long long q = kbase + k;
-            const bool v = gval && q < kend;
+            const bool v = L.gv && q < kend;
             const bf16 *src = o.p;
             if (v) {
                 long long pix = q;
-                if (o.kind == SUR_OP_TCONV3) pix = nb_pixel(q, tap, o.lh, o.lw);
-                else if (o.kind == SUR_OP_TUP) pix = fine_pixel(q, tap, o.lh, o.lw);
-                src = o.p + pix * o.ld + o.c0 + c;
+                if (o.kind != SUR_OP_TDENSE) {
+                    const int x = (int)(q & ((1 << o.lw) - 1)), yb = (int)(q >> o.lw);
+                    pix = o.kind == SUR_OP_TCONV3 ? shifted(x, yb, L.dy, L.dx, o.lh, o.lw)
+                                                  : child(x, yb, L.dy, L.dx, o.lw);
+                }
+                src = o.p + pix * o.ld + o.c0 + L.c;
             }
-            cp_async16(s + (uint32_t)(((k >> 3) * G + g) * 128 + (k & 7) * 16), src, v);
+            cp_async16(s + (uint32_t)(((k >> 3) * G + L.g) * 128 + (k & 7) * 16), src, v);
         }
     }
 }
@@ -177,14 +241,40 @@ __device__ __forceinline__ void store32_bf16(bf16 *dst, const float *v)
     for (int i = 0; i < 4; ++i) d[i] = pack8(v + 8 * i);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar));
+}
+
+// Bounded wait that also gives up as soon as another role raised the abort flag.
+__device__ __forceinline__ bool mbar_wait_abortable(uint32_t bar, uint32_t parity, const volatile int *abort_flag)
+{
+    uint32_t done = 0;
+    for (long it = 0; it < kWaitLimit && !done; ++it) {
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.b32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity));
+        if (!done && (it & 63) == 63 && *abort_flag) return false;
+    }
+    return done != 0;
+}
+
+// Warp-specialised GEMM CTA: warps 0-3 produce stages (cp.async) and afterwards
+// run the epilogue; warp 4 issues the MMAs.
+//   full[s]  (128 arrivals): the producers' copies of stage s have landed and are
+//            fenced for the async proxy;
+//   empty[s] (tcgen05.commit): the MMAs that read stage s have completed;
+//   done     (tcgen05.commit): every MMA of the tile has completed.
 template <int BN>
-__global__ void __launch_bounds__(128, 1) k_gemm(const KArgs g)
+__global__ void __launch_bounds__(160, 1) k_gemm(const KArgs g)
 {
     using C = Cfg<BN>;
     constexpr int NS = C::NS;
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ __align__(8) uint64_t mbar[NS];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], done_bar;
     __shared__ uint32_t tmem_sh;
+    __shared__ int abort_flag;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const long long m0 = (long long)blockIdx.x * BM;
     const int n0 = blockIdx.y * BN;
@@ -193,6 +283,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const KArgs g)
     if (kend > g.K) kend = g.K;
     const int nkb = kend > kbeg ? (int)((kend - kbeg + BK - 1) / BK) : 0;
     const bool a_mn = g.a.kind >= SUR_OP_TDENSE, b_mn = g.b.kind >= SUR_OP_TDENSE;
+    volatile int *abort_v = &abort_flag;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
@@ -200,57 +291,118 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const KArgs g)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (t == 0) {
-        for (int s = 0; s < NS; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[s])), "r"(1));
+        for (int s = 0; s < NS; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(128));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&done_bar)), "r"(1));
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_sh;
-    // Instruction descriptor: FP32 accumulator, BF16 A and B, transpose flags for
-    // MN-major operands, N >> 3, M >> 4.
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
-                           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     const uint32_t sbase = smem_u32(dsm);
 
-    auto stage_load = [&](int kb) {
-        const uint32_t sa = sbase + (uint32_t)((kb % NS) * C::STAGE);
-        load_tile<BM>(g.a, sa, m0, kbeg + (long long)kb * BK, kend, t);
-        load_tile<BN>(g.b, sa + C::A_BYTES, n0, kbeg + (long long)kb * BK, kend, t);
-    };
-
-    bool ok = true;
-    uint32_t phase_bits = 0;   // parity of the next completion of each stage's barrier
-    int issued = 0;            // MMA groups committed
-    int waited = 0;            // MMA groups known complete
-    // Prologue: NS - 1 K blocks in flight.
-    for (int kb = 0; kb < NS - 1; ++kb) {
-        if (kb < nkb) stage_load(kb);
-        asm volatile("cp.async.commit_group;");
-    }
-    for (int kb = 0; kb < nkb; ++kb) {
-        // Refill the stage that MMA group kb-1 read with K block kb + NS - 1.
-        const int nxt = kb + NS - 1;
-        if (nxt < nkb) {
-            while (waited < issued && waited <= kb - 1) {
-                const int s = waited % NS;
-                if (!mbar_wait(smem_u32(&mbar[s]), (phase_bits >> s) & 1u)) ok = false;
-                phase_bits ^= 1u << s;
-                ++waited;
+    if (warp < 4) {
+        // ---------------- producers ----------------
+        Loader<BM> La;
+        Loader<BN> Lb;
+        loader_init<BM>(g.a, La, m0, t);
+        loader_init<BN>(g.b, Lb, n0, t);
+        bool ok = true;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = kb % NS;
+            if (kb >= NS && !mbar_wait_abortable(smem_u32(&empty[s]), ((kb / NS) - 1) & 1, abort_v)) {
+                ok = false;
+                *abort_v = 1;
+                break;
             }
-            if (ok) stage_load(nxt);
+            const uint32_t sa = sbase + (uint32_t)(s * C::STAGE);
+            const long long kbase = kbeg + (long long)kb * BK;
+            load_tile<BM>(g.a, La, sa, kbase, kend, t);
+            load_tile<BN>(g.b, Lb, sa + C::A_BYTES, kbase, kend, t);
+            // Arrives on full[s] once this thread's copies above have landed.
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[s])));
         }
-        asm volatile("cp.async.commit_group;");
-        asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1));
-        asm volatile("fence.proxy.async.shared::cta;");
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
+        asm volatile("cp.async.wait_all;");
+        // ---------------- epilogue ----------------
+        const bool fin = mbar_wait(smem_u32(&done_bar), 0);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!fin) *abort_v = 1;
+        __syncwarp();
+        // Warp-uniform decision: tcgen05.ld below is a .sync.aligned warp instruction.
+        const bool good = __all_sync(0xffffffffu, fin && !*abort_v && nkb > 0);
+        if (good) {
+            const long long row = m0 + warp * 32 + lane;
+            const bool rv = row < g.M;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (!rv) continue;
+                const int col = n0 + c0;
+                float v[32];
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) v[jj] = __uint_as_float(r[jj]);
+                if (g.epi == SUR_EPI_F32_ATOMIC) {
+                    float *o = static_cast<float *>(g.out) + row * g.ldo + g.co0 + col;
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) atomicAdd(o + jj, v[jj]);
+                } else if (g.epi == SUR_EPI_SHUF) {
+                    const int sidx = col / g.shuf_cout, c = col - sidx * g.shuf_cout;
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) v[jj] += g.bias[c + jj];
+                    const long long q = fine_pixel(row, sidx, g.shuf_lh, g.shuf_lw);
+                    store32_bf16(g.y + q * g.ldy + g.cy0 + c, v);
+                } else {
+                    if (g.bias) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) v[jj] += g.bias[col + jj];
+                    }
+                    if (g.epi == SUR_EPI_F32) {
+                        float4 *o =
+                            reinterpret_cast<float4 *>(static_cast<float *>(g.out) + row * g.ldo + g.co0 + col);
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj)
+                            o[jj] = make_float4(v[4 * jj], v[4 * jj + 1], v[4 * jj + 2], v[4 * jj + 3]);
+                    } else {
+                        if (g.out) store32_bf16(static_cast<bf16 *>(g.out) + row * g.ldo + g.co0 + col, v);
+                        if (g.epi == SUR_EPI_CONV) {
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj) v[jj] = silu(v[jj]);
+                            store32_bf16(g.y + row * g.ldy + g.cy0 + col, v);
+                        }
+                    }
+                }
+            }
         }
-        if (t == 0) {
+    } else if (lane == 0) {
+        // ---------------- MMA issuer (warp 4, one thread) ----------------
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) |
+                               ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % NS;
+            if (!mbar_wait_abortable(smem_u32(&full[s]), (kb / NS) & 1, abort_v)) {
+                *abort_v = 1;
+                break;
+            }
+            // The stage was written through the generic proxy (cp.async) and is read
+            // by the tensor core through the async proxy.
+            asm volatile("fence.proxy.async.shared::cta;");
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t sa = sbase + (uint32_t)((kb % NS) * C::STAGE), sb = sa + C::A_BYTES;
+            const uint32_t sa = sbase + (uint32_t)(s * C::STAGE), sb = sa + C::A_BYTES;
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k) {
                 const uint64_t da =
@@ -263,77 +415,15 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const KArgs g)
                              "l"(da), "l"(db), "r"(idesc), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mbar[kb % NS])));
+                smem_u32(&empty[s])));
         }
-        ++issued;
-    }
-    // Drain every committed MMA group (also on the error path, so that tensor
-    // memory is idle before it is read or freed).
-    while (waited < issued) {
-        const int s = waited % NS;
-        if (!mbar_wait(smem_u32(&mbar[s]), (phase_bits >> s) & 1u)) ok = false;
-        phase_bits ^= 1u << s;
-        ++waited;
-    }
-    asm volatile("cp.async.wait_group 0;");
-    ok = __syncthreads_and(ok);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok && nkb > 0) {
-        const long long row = m0 + warp * 32 + lane;
-        const bool rv = row < g.M;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (!rv) continue;
-            const int col = n0 + c0;
-            float v[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-            if (g.epi == SUR_EPI_F32_ATOMIC) {
-                float *o = static_cast<float *>(g.out) + row * g.ldo + g.co0 + col;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) atomicAdd(o + j, v[j]);
-            } else if (g.epi == SUR_EPI_SHUF) {
-                const int sidx = col / g.shuf_cout, c = col - sidx * g.shuf_cout;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] += g.bias[c + j];
-                const long long q = fine_pixel(row, sidx, g.shuf_lh, g.shuf_lw);
-                store32_bf16(g.y + q * g.ldy + g.cy0 + c, v);
-            } else {
-                if (g.bias) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] += g.bias[col + j];
-                }
-                if (g.epi == SUR_EPI_F32) {
-                    float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(g.out) + row * g.ldo + g.co0 + col);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                } else {
-                    if (g.out) store32_bf16(static_cast<bf16 *>(g.out) + row * g.ldo + g.co0 + col, v);
-                    if (g.epi == SUR_EPI_CONV) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = silu(v[j]);
-                        store32_bf16(g.y + row * g.ldy + g.cy0 + col, v);
-                    }
-                }
-            }
-        }
-    } else if (!ok && t == 0) {
-        atomicExch(g.status, 1);
+        // Arrives once every MMA issued above has completed (at once if none was issued).
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&done_bar)));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (t == 0 && *abort_v) atomicExch(g.status, 1);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
 }
@@ -351,7 +441,7 @@ cudaError_t launch_gemm(const KArgs &g, long long mtiles, int splits, cudaStream
         attr_dev = dev;
     }
     const dim3 grid((unsigned)mtiles, (unsigned)(g.N / BN), (unsigned)splits);
-    k_gemm<BN><<<grid, 128, Cfg<BN>::SMEM, st>>>(g);
+    k_gemm<BN><<<grid, 160, Cfg<BN>::SMEM, st>>>(g);
     return cudaGetLastError();
 }
 
