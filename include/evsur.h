@@ -39,26 +39,36 @@ enum { SUR_OK = 0, SUR_EINVAL = 1, SUR_ECUDA = 2, SUR_ENOMEM = 3, SUR_ETIMEOUT =
  * networks).  All matrices are BF16 unless stated.
  * ------------------------------------------------------------------------- */
 
-/* Operand kinds of the tensor-core GEMM C[m][n] = sum_k A(m, k) B(n, k).
+/* Halo-padded NHWC storage.  A tensor of B images on an H x W periodic grid
+ * (H, W powers of two) is stored as [B][H+2][W+2][ld] BF16: interior pixel
+ * (b, y, x) at [b][y+1][x+1]; rows 0 and H+1 and columns 0 and W+1 hold the
+ * periodic copies of rows H-1, 0 and columns W-1, 0.  Pixel index
+ * q = (b*H + y)*W + x counts interior pixels; pix(q) is its stored position.
  *
- *  SUR_OP_DENSE   X(r, k) = p[r*ld + c0 + k]                      (row-major)
- *  SUR_OP_CONV3   X(r, k) = p[nb(r, tap)*ld + c0 + c]  with k = tap*C + c,
- *                 tap = (dy+1)*3 + (dx+1), nb(r, tap) the periodic neighbour
- *                 (y+dy, x+dx) of pixel r on an H x W grid; k >= 9C reads 0.
- *                 (Implicit im2col of a 3x3 periodic convolution.)
- *  SUR_OP_UPADJ   X(r, k) = p[fine(r, s)*ld + c0 + c]  with k = s*C + c, r a
- *                 pixel of the coarse H x W grid and fine(r, s) its child
- *                 (2y + s/2, 2x + s%2) on the 2H x 2W grid; k >= 4C reads 0.
- *  SUR_OP_TDENSE  X(r, k) = p[k*ld + c0 + r]                      (transposed)
- *  SUR_OP_TCONV3  X(r, k) = p[nb(k, tap)*ld + c0 + c]  with r = tap*C + c
- *  SUR_OP_TUP     X(r, k) = p[fine(k, s)*ld + c0 + c]  with r = s*C + c
+ * Operand kinds of the tensor-core GEMM C[m][n] = sum_k A(m, k) B(n, k):
  *
- * Rows r >= rows and K indices k >= K read zero.  C, H and W are powers of
- * two, C >= 8; ld and c0 are multiples of 8 elements and p is 16-byte aligned.
- * Memory is read in 8-element chunks: a DENSE operand needs c0 + K rounded up
- * to 8 <= ld, a TDENSE operand c0 + rows rounded up to 8 <= ld, and a gather
- * kind c0 + C <= ld (SUR_EINVAL otherwise). */
-enum { SUR_OP_DENSE = 0, SUR_OP_CONV3 = 1, SUR_OP_UPADJ = 2, SUR_OP_TDENSE = 3, SUR_OP_TCONV3 = 4, SUR_OP_TUP = 5 };
+ *  SUR_OP_DENSE   X(r, k) = p[r*ld + c0 + k]                   (row-major matrix)
+ *  SUR_OP_PIX     X(r, k) = p[pix(r)*ld + c0 + k],  k < C       (pixel rows)
+ *  SUR_OP_CONV3   X(r, k) = p[(pix(r) + dy*(W+2) + dx)*ld + c0 + c]  with
+ *                 k = tap*C + c, tap = (dy+1)*3 + (dx+1); k >= 9C reads 0
+ *                 (implicit im2col of a periodic 3x3 convolution)
+ *  SUR_OP_UPADJ   X(r, k) = p[fine(r, s)*ld + c0 + c]  with k = s*C + c, r an
+ *                 interior pixel of the coarse H x W grid, fine(r, s) the stored
+ *                 position of its child (2y + s/2, 2x + s%2) on the padded
+ *                 2H x 2W grid; k >= 4C reads 0
+ *  SUR_OP_TPIX    X(r, k) = p[pix(k)*ld + c0 + r]               (pixels along K)
+ *  SUR_OP_TCONV3  X(r, k) = p[(pix(k) + dy*(W+2) + dx)*ld + c0 + c],  r = tap*C + c
+ *  SUR_OP_TUP     X(r, k) = p[fine(k, s)*ld + c0 + c],  r = s*C + c
+ *
+ * Rows r >= rows and K indices k >= K read zero.  C >= 8 is a power of two; ld
+ * and c0 are multiples of 8 elements and p is 16-byte aligned.  Memory is read
+ * in 8-element chunks: a DENSE operand needs c0 + K rounded up to 8 <= ld, a
+ * TPIX operand c0 + rows rounded up to 8 <= ld, and the other kinds
+ * c0 + C <= ld (SUR_EINVAL otherwise). */
+enum {
+    SUR_OP_DENSE = 0, SUR_OP_PIX = 1, SUR_OP_CONV3 = 2, SUR_OP_UPADJ = 3,
+    SUR_OP_TPIX = 4, SUR_OP_TCONV3 = 5, SUR_OP_TUP = 6
+};
 
 typedef struct sur_operand {
     const void *p; /* device, BF16 */
@@ -71,14 +81,18 @@ typedef struct sur_operand {
 
 /* Epilogues.  acc is the FP32 accumulator of C[m][n]; bias (FP32, may be NULL
  * except for SUR_EPI_CONV and SUR_EPI_SHUF) is indexed by n (by n % cout for SHUF).
- *  SUR_EPI_BF16        out[m*ldo + co0 + n] = bf16(acc + bias)
- *  SUR_EPI_F32         out[m*ldo + co0 + n] = acc + bias           (FP32 out)
- *  SUR_EPI_F32_ATOMIC  out[m*ldo + co0 + n] += acc                 (FP32 out, split-K)
- *  SUR_EPI_CONV        z = acc + bias; out[...] = bf16(z) (skipped when out is NULL),
- *                      y[m*ldy + cy0 + n] = bf16(silu(z)),  silu(z) = z / (1 + e^-z)
- *  SUR_EPI_SHUF        2x2 stride-2 transposed convolution: n = s*cout + c,
- *                      y[fine(m, s)*ldy + cy0 + c] = bf16(acc + bias[c]) on the
- *                      2H x 2W grid of the coarse grid (shuf_H, shuf_W) of m. */
+ * When A's rows are pixels (PIX, CONV3, UPADJ) the output rows are pixels of
+ * A's grid and row m is stored at pix(m) of a halo-padded output; otherwise at m.
+ *  SUR_EPI_BF16        out[row(m)*ldo + co0 + n] = bf16(acc + bias)
+ *  SUR_EPI_F32         out[row(m)*ldo + co0 + n] = acc + bias        (FP32 out)
+ *  SUR_EPI_F32_ATOMIC  out[m*ldo + co0 + n] += acc                   (FP32 out, split-K)
+ *  SUR_EPI_CONV        z = acc + bias; out[row(m)...] = bf16(z) (skipped when out is
+ *                      NULL); y[...*ldy + cy0 + n] = bf16(silu(z)), silu(z) = z/(1+e^-z),
+ *                      written at pix(m) and at its periodic halo copies
+ *  SUR_EPI_SHUF        2x2 stride-2 transposed convolution (A's rows are pixels of
+ *                      the coarse grid): n = s*cout + c, y at the child s of m on
+ *                      the padded 2H x 2W grid (and its halo copies):
+ *                      bf16(acc + bias[c]). */
 enum { SUR_EPI_BF16 = 0, SUR_EPI_F32 = 1, SUR_EPI_F32_ATOMIC = 2, SUR_EPI_CONV = 3, SUR_EPI_SHUF = 4 };
 
 typedef struct sur_gemm_args {
@@ -91,13 +105,19 @@ typedef struct sur_gemm_args {
     int ldo, co0;
     void *y;           /* BF16, SUR_EPI_CONV / SUR_EPI_SHUF */
     int ldy, cy0;
-    int shuf_cout, shuf_H, shuf_W;
+    int shuf_cout;
 } sur_gemm_args;
 
 /* One GEMM on the tensor cores (128 x {32,64,128} CTA tiles, 64-deep K blocks,
- * 3-4 stage cp.async pipeline, one thread issuing tcgen05.mma into a TMEM
- * accumulator).  d_status (device int) is set to 1 if a wait gave up. */
+ * one thread issuing tcgen05.mma into a TMEM accumulator).  A CONV3 or PIX A
+ * operand with a DENSE B operand and no split is fed by TMA (swizzled
+ * cp.async.bulk.tensor boxes); every other form by a cp.async pipeline.
+ * d_status (device int) is set to 1 if a wait gave up. */
 int sur_gemm(const sur_gemm_args *g, int *d_status, void *stream);
+
+/* 0 routes every GEMM through the cp.async pipeline (for testing both paths);
+ * 1 (the default) lets eligible GEMMs use TMA.  Process-wide. */
+int sur_set_tma(int enable);
 
 /* ---------------------------------------------------------------------------
  * The model.

@@ -106,6 +106,10 @@ int cuda_fail(sur_model *m, cudaError_t e, const char *where)
 int lvl_h(const sur_model *m, int l) { return m->H >> l; }
 int lvl_w(const sur_model *m, int l) { return m->W >> l; }
 long long lvl_pix(const sur_model *m, int l, int B) { return (long long)B * lvl_h(m, l) * lvl_w(m, l); }
+// Stored (halo-padded) pixel count of level l.
+long long lvl_pad(const sur_model *m, int l, int B) { return (long long)B * (lvl_h(m, l) + 2) * (lvl_w(m, l) + 2); }
+int lvl_lh(const sur_model *m, int l) { return m->lh - l; }
+int lvl_lw(const sur_model *m, int l) { return m->lw - l; }
 
 sur_operand dense(const void *p, int ld, int c0, long long rows)
 {
@@ -173,7 +177,7 @@ int up_fwd(sur_model *m, int j, int B, const bf16 *Xc, bf16 *cat)
     const int l = kUpLevel[j];
     const long long Mc = lvl_pix(m, l, B);
     sur_gemm_args g{};
-    g.a = dense(Xc, U.cin, 0, Mc);
+    g.a = gather(SUR_OP_PIX, Xc, U.cin, 0, U.cin, Mc, lvl_h(m, l), lvl_w(m, l));
     g.b = dense(U.wb, U.cin, 0, 4 * U.cout);
     g.M = (int)Mc;
     g.N = 4 * U.cout;
@@ -185,8 +189,6 @@ int up_fwd(sur_model *m, int j, int B, const bf16 *Xc, bf16 *cat)
     g.ldy = 2 * U.cout;
     g.cy0 = U.cout;
     g.shuf_cout = U.cout;
-    g.shuf_H = lvl_h(m, l);
-    g.shuf_W = lvl_w(m, l);
     return evsur::gemm(g, m->status, m->stream);
 }
 
@@ -197,12 +199,11 @@ int conv_bwd(sur_model *m, int i, int B, const bf16 *X, int ldx, const bf16 *dY,
     const int l = kConvLevel[i];
     const long long M = lvl_pix(m, l, B);
     const int H = lvl_h(m, l), W = lvl_w(m, l);
-    CK(evsur::silu_bwd(dY, ldd, m->Z[i], M, L.cout, m->dZ, m->stream));
-    CK(evsur::colsum(m->dZ, L.cout, M, L.cout, m->G + L.b, m->stream));
+    CK(evsur::silu_bwd(dY, ldd, m->Z[i], M, lvl_lh(m, l), lvl_lw(m, l), L.cout, m->dZ, m->stream));
+    CK(evsur::colsum(m->dZ, L.cout, M, lvl_lh(m, l), lvl_lw(m, l), L.cout, m->G + L.b, m->stream));
     sur_gemm_args g{};
     g.a = gather(SUR_OP_TCONV3, X, ldx, 0, L.cin, 9LL * L.cin, H, W);
-    g.b = dense(m->dZ, L.cout, 0, L.cout);
-    g.b.kind = SUR_OP_TDENSE;
+    g.b = gather(SUR_OP_TPIX, m->dZ, L.cout, 0, 0, L.cout, H, W);
     g.M = L.kp;
     g.N = L.cout;
     g.K = (int)M;
@@ -236,11 +237,11 @@ int up_bwd(sur_model *m, int j, int B, const bf16 *Xc, const bf16 *dcat, bf16 *d
     const int l = kUpLevel[j];
     const long long Mc = lvl_pix(m, l, B);
     const int H = lvl_h(m, l), W = lvl_w(m, l);
-    CK(evsur::colsum(dcat + U.cout, 2 * U.cout, 4 * Mc, U.cout, m->G + U.b, m->stream));
+    CK(evsur::colsum(dcat + U.cout, 2 * U.cout, 4 * Mc, lvl_lh(m, l - 1), lvl_lw(m, l - 1), U.cout, m->G + U.b,
+                     m->stream));
     sur_gemm_args g{};
     g.a = gather(SUR_OP_TUP, dcat, 2 * U.cout, U.cout, U.cout, 4LL * U.cout, H, W);
-    g.b = dense(Xc, U.cin, 0, U.cin);
-    g.b.kind = SUR_OP_TDENSE;
+    g.b = gather(SUR_OP_TPIX, Xc, U.cin, 0, 0, U.cin, H, W);
     g.M = 4 * U.cout;
     g.N = U.cin;
     g.K = (int)Mc;
@@ -289,7 +290,9 @@ int ensure_batch(sur_model *m, int B, bool train)
         m->arena = nullptr;
         m->cap = 0;
     }
-    const long long M0 = lvl_pix(m, 0, B), M1 = lvl_pix(m, 1, B), M2 = lvl_pix(m, 2, B), M3 = lvl_pix(m, 3, B);
+    // NHWC tensors are stored halo-padded; the planar FP32 fields are not.
+    const long long M0 = lvl_pad(m, 0, B), M1 = lvl_pad(m, 1, B), M2 = lvl_pad(m, 2, B), M3 = lvl_pad(m, 3, B);
+    const long long F0 = lvl_pix(m, 0, B);
     struct Req {
         void **dst;
         long long bytes;
@@ -315,10 +318,10 @@ int ensure_batch(sur_model *m, int B, bool train)
     bf(&m->Y13, M1 * 64);
     bf(&m->Y02, M0 * 32);
     bf(&m->Y03, M0 * 32);
-    fl(&m->next, 4 * M0);
+    fl(&m->next, 4 * F0);
     if (train) {
-        for (int i = 0; i < kConvs; ++i) bf(&m->Z[i], lvl_pix(m, kConvLevel[i], B) * m->conv[i].cout);
-        fl(&m->dO, 4 * M0);
+        for (int i = 0; i < kConvs; ++i) bf(&m->Z[i], lvl_pad(m, kConvLevel[i], B) * m->conv[i].cout);
+        fl(&m->dO, 4 * F0);
         bf(&m->dZ, M0 * 32);
         bf(&m->dY03, M0 * 32);
         bf(&m->dY02, M0 * 32);
@@ -357,7 +360,7 @@ int ensure_batch(sur_model *m, int B, bool train)
 int forward(sur_model *m, const float *d_x, int B, bool train)
 {
     const long long M0 = lvl_pix(m, 0, B);
-    CK(evsur::pack_in(d_x, M0, m->norm, m->xin, m->stream));
+    CK(evsur::pack_in(d_x, M0, m->lh, m->lw, m->norm, m->xin, m->stream));
     int rc;
 #define F(expr)                  \
     if ((rc = (expr)) != SUR_OK) \
@@ -390,7 +393,7 @@ int forward(sur_model *m, const float *d_x, int B, bool train)
 int backward(sur_model *m, int B)
 {
     const long long M0 = lvl_pix(m, 0, B);
-    CK(evsur::head_bwd(m->Y03, M0, m->P + m->head_w, m->dO, m->dY03, m->G + m->head_w, m->G + m->head_b, m->stream));
+    CK(evsur::head_bwd(m->Y03, M0, m->lh, m->lw, m->P + m->head_w, m->dO, m->dY03, m->G + m->head_w, m->G + m->head_b, m->stream));
     int rc;
 #define BW(expr)                 \
     if ((rc = (expr)) != SUR_OK) \
@@ -440,7 +443,7 @@ int fwd_bwd(sur_model *m, const float *d_x, const float *d_y, int B, float *loss
     CK(cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream));
     if ((rc = forward(m, d_x, B, true))) return rc;
     const long long M0 = lvl_pix(m, 0, B);
-    CK(evsur::head(m->Y03, M0, m->P + m->head_w, m->P + m->head_b, m->norm, d_x, d_y, 0, m->dO, m->loss, nullptr,
+    CK(evsur::head(m->Y03, M0, m->lh, m->lw, m->P + m->head_w, m->P + m->head_b, m->norm, d_x, d_y, 0, m->dO, m->loss, nullptr,
                    m->stream));
     if ((rc = backward(m, B))) return rc;
     if (loss) {
@@ -670,7 +673,7 @@ int sur_infer(sur_model *m, const float *d_x, float *d_y, int batch)
     if (rc) return rc;
     if ((rc = forward(m, d_x, batch, false))) return rc;
     const long long M0 = lvl_pix(m, 0, batch);
-    CK(evsur::head(m->Y03, M0, m->P + m->head_w, m->P + m->head_b, m->norm, d_x, nullptr, 1, nullptr, nullptr, d_y,
+    CK(evsur::head(m->Y03, M0, m->lh, m->lw, m->P + m->head_w, m->P + m->head_b, m->norm, d_x, nullptr, 1, nullptr, nullptr, d_y,
                    m->stream));
     return SUR_OK;
 }
@@ -698,7 +701,7 @@ int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur
     bool lb_current = false;
     for (int w = 0; w < cfg->windows; ++w) {
         if ((rc = forward(m, d_fields, batch, false))) return rc;
-        CK(evsur::head(m->Y03, N, m->P + m->head_w, m->P + m->head_b, m->norm, d_fields, nullptr, 1, nullptr,
+        CK(evsur::head(m->Y03, N, m->lh, m->lw, m->P + m->head_w, m->P + m->head_b, m->norm, d_fields, nullptr, 1, nullptr,
                        nullptr, m->next, m->stream));
         CK(evsur::indicators(m->next, batch, Mb, cfg->rho_mid, m->ind, m->status + 1, m->stream));
         CK(cudaMemcpyAsync(nxt.data(), m->ind, sizeof(double) * 2 * batch, cudaMemcpyDeviceToHost, m->stream));

@@ -15,7 +15,7 @@ import numpy as np
 from . import lib as _lib_loader
 
 SUR_OK, SUR_EINVAL, SUR_ECUDA, SUR_ENOMEM, SUR_ETIMEOUT = 0, 1, 2, 3, 4
-SUR_OP_DENSE, SUR_OP_CONV3, SUR_OP_UPADJ, SUR_OP_TDENSE, SUR_OP_TCONV3, SUR_OP_TUP = range(6)
+SUR_OP_DENSE, SUR_OP_PIX, SUR_OP_CONV3, SUR_OP_UPADJ, SUR_OP_TPIX, SUR_OP_TCONV3, SUR_OP_TUP = range(7)
 SUR_EPI_BF16, SUR_EPI_F32, SUR_EPI_F32_ATOMIC, SUR_EPI_CONV, SUR_EPI_SHUF = range(5)
 
 _ERRNAMES = {SUR_EINVAL: "SUR_EINVAL", SUR_ECUDA: "SUR_ECUDA", SUR_ENOMEM: "SUR_ENOMEM",
@@ -23,7 +23,7 @@ _ERRNAMES = {SUR_EINVAL: "SUR_EINVAL", SUR_ECUDA: "SUR_ECUDA", SUR_ENOMEM: "SUR_
 
 # Every symbol include/evsur.h declares.
 EXPORTED_SYMBOLS = (
-    "sur_gemm", "sur_init", "sur_free", "sur_num_params", "sur_get_params", "sur_set_params", "sur_get_grads",
+    "sur_gemm", "sur_set_tma", "sur_init", "sur_free", "sur_num_params", "sur_get_params", "sur_set_params", "sur_get_grads",
     "sur_set_norm", "sur_forward_backward", "sur_train_step", "sur_infer", "sur_indicators", "sur_rollout",
     "sur_last_error",
 )
@@ -51,8 +51,7 @@ class sur_gemm_args(ctypes.Structure):
     _fields_ = [("a", sur_operand), ("b", sur_operand), ("M", ctypes.c_int), ("N", ctypes.c_int),
                 ("K", ctypes.c_int), ("splits", ctypes.c_int), ("epi", ctypes.c_int),
                 ("bias", ctypes.c_void_p), ("out", ctypes.c_void_p), ("ldo", ctypes.c_int), ("co0", ctypes.c_int),
-                ("y", ctypes.c_void_p), ("ldy", ctypes.c_int), ("cy0", ctypes.c_int), ("shuf_cout", ctypes.c_int),
-                ("shuf_H", ctypes.c_int), ("shuf_W", ctypes.c_int)]
+                ("y", ctypes.c_void_p), ("ldy", ctypes.c_int), ("cy0", ctypes.c_int), ("shuf_cout", ctypes.c_int)]
 
 
 class sur_rollout_cfg(ctypes.Structure):
@@ -71,6 +70,7 @@ def lib():
         if not _ready:
             vp, ip, fp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float)
             L.sur_gemm.argtypes = [ctypes.POINTER(sur_gemm_args), vp, vp]
+            L.sur_set_tma.argtypes = [ip]
             L.sur_init.argtypes = [ip, ip, ip, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
             L.sur_free.argtypes = [vp]
             L.sur_num_params.argtypes = [vp]
@@ -109,6 +109,10 @@ def _f32(a):
 
 def sur_gemm(args: sur_gemm_args, d_status, stream=0):
     _check(lib().sur_gemm(ctypes.byref(args), d_status, stream))
+
+
+def sur_set_tma(enable):
+    _check(lib().sur_set_tma(1 if enable else 0))
 
 
 def sur_init(H, W, base_ch=BASE, seed=0, stream=0):

@@ -35,6 +35,10 @@ def bf(a):
     return t, t.float().cpu().numpy().astype(np.float64)
 
 
+def bf16_round(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
 def op(t, kind, ld, c0=0, C=0, rows=0, H=0, W=0):
     return S.sur_operand(t.data_ptr(), kind, ld, c0, C, rows, H, W)
 
@@ -47,7 +51,7 @@ def run(args):
 
 
 def gemm(a, b, M, N, K, epi=S.SUR_EPI_F32, out=None, ldo=0, co0=0, bias=None, y=None, ldy=0, cy0=0, splits=1,
-         shuf=(0, 0, 0)):
+         shuf=0):
     g = S.sur_gemm_args()
     g.a, g.b, g.M, g.N, g.K, g.splits, g.epi = a, b, M, N, K, splits, epi
     g.bias = bias.data_ptr() if bias is not None else None
@@ -55,13 +59,29 @@ def gemm(a, b, M, N, K, epi=S.SUR_EPI_F32, out=None, ldo=0, co0=0, bias=None, y=
     g.ldo, g.co0 = ldo, co0
     g.y = y.data_ptr() if y is not None else None
     g.ldy, g.cy0 = ldy, cy0
-    g.shuf_cout, g.shuf_H, g.shuf_W = shuf
+    g.shuf_cout = shuf
     run(g)
 
 
 def close(c, ref, absref, tol=2e-6):
     err = np.abs(c - ref)
     assert np.all(err <= tol * absref + 1e-30), float((err / (absref + 1e-30)).max())
+
+
+def padded(x):
+    """Halo-padded NHWC copy (periodic halo of one pixel)."""
+    return np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0)), mode="wrap")
+
+
+def interior(a):
+    return a[:, 1:-1, 1:-1, :]
+
+
+@pytest.fixture(params=[True, False], ids=["tma", "cpasync"])
+def tma(request):
+    S.sur_set_tma(request.param)
+    yield request.param
+    S.sur_set_tma(True)
 
 
 def test_dense_ragged():
@@ -73,87 +93,99 @@ def test_dense_ragged():
     close(out.cpu().numpy(), Ad @ Bd.T, np.abs(Ad) @ np.abs(Bd).T)
 
 
-@pytest.mark.parametrize("Cin,Cout,c0,ld", [(32, 64, 0, 32), (8, 32, 8, 16), (256, 128, 0, 256)])
-def test_conv3_gather(Cin, Cout, c0, ld):
-    Bn, H, W = 2, 16, 32
-    X, Xd = bf(gen.normal(size=(Bn, H, W, ld)))
+@pytest.mark.parametrize("Cin,Cout,c0,ld,H,W", [(32, 64, 0, 32, 16, 32), (8, 32, 8, 16, 16, 32),
+                                                 (256, 128, 0, 256, 16, 32), (64, 32, 0, 64, 256, 256),
+                                                 (128, 64, 0, 128, 4, 8)])
+def test_conv3_gather(Cin, Cout, c0, ld, H, W, tma):
+    Bn = 2 if H * W < 65536 else 1
+    x = bf16_round(gen.normal(size=(Bn, H, W, ld)))
+    X, _ = bf(padded(x))
     Wt, Wd = bf(gen.normal(size=(9, Cin, Cout)) / np.sqrt(9 * Cin))
     kp = U.kp_of(Cin)
     Wb = torch.zeros(Cout, kp, dtype=torch.bfloat16, device=dev)
     Wb[:, :9 * Cin] = Wt.reshape(9 * Cin, Cout).t()
     M = Bn * H * W
-    out = torch.full((M, Cout), float("nan"), device=dev)
+    out = torch.full((Bn, H + 2, W + 2, Cout), float("nan"), device=dev)
     gemm(op(X, S.SUR_OP_CONV3, ld, c0, Cin, M, H, W), op(Wb, S.SUR_OP_DENSE, kp, rows=Cout), M, Cout, kp,
          out=out, ldo=Cout)
-    x = Xd[..., c0:c0 + Cin]
-    ref = U.conv3(x, Wd, np.zeros(Cout)).reshape(M, Cout)
-    absref = U.conv3(np.abs(x), np.abs(Wd), np.zeros(Cout)).reshape(M, Cout)
-    close(out.cpu().numpy(), ref, absref)
+    xs = x[..., c0:c0 + Cin]
+    ref = U.conv3(xs, Wd, np.zeros(Cout))
+    absref = U.conv3(np.abs(xs), np.abs(Wd), np.zeros(Cout))
+    close(interior(out.cpu().numpy()), ref, absref)
 
 
-def test_conv_epilogue_bias_silu_into_slice():
+def test_conv_epilogue_bias_silu_halo(tma):
     Bn, H, W, Cin, Cout = 1, 32, 16, 32, 32
-    X, Xd = bf(gen.normal(size=(Bn, H, W, Cin)))
+    x = bf16_round(gen.normal(size=(Bn, H, W, Cin)))
+    X, _ = bf(padded(x))
     Wt, Wd = bf(gen.normal(size=(9, Cin, Cout)) / np.sqrt(9 * Cin))
     bias = torch.tensor(gen.normal(size=Cout), dtype=torch.float32, device=dev)
     kp = U.kp_of(Cin)
     Wb = torch.zeros(Cout, kp, dtype=torch.bfloat16, device=dev)
     Wb[:, :9 * Cin] = Wt.reshape(9 * Cin, Cout).t()
     M = Bn * H * W
-    Z = torch.zeros(M, Cout, dtype=torch.bfloat16, device=dev)
-    Y = torch.full((M, 2 * Cout), 7.0, dtype=torch.bfloat16, device=dev)
+    Z = torch.zeros(Bn, H + 2, W + 2, Cout, dtype=torch.bfloat16, device=dev)
+    Y = torch.full((Bn, H + 2, W + 2, 2 * Cout), 7.0, dtype=torch.bfloat16, device=dev)
     gemm(op(X, S.SUR_OP_CONV3, Cin, 0, Cin, M, H, W), op(Wb, S.SUR_OP_DENSE, kp, rows=Cout), M, Cout, kp,
          epi=S.SUR_EPI_CONV, out=Z, ldo=Cout, bias=bias, y=Y, ldy=2 * Cout, cy0=0)
-    z = U.conv3(Xd, Wd, bias.cpu().numpy().astype(np.float64)).reshape(M, Cout)
-    zg = Z.float().cpu().numpy()
+    z = U.conv3(x, Wd, bias.cpu().numpy().astype(np.float64))
+    zg = interior(Z.float().cpu().numpy())
     assert np.all(np.abs(zg - z) <= 2 ** -8 * np.abs(z) + 1e-5)
     yg = Y.float().cpu().numpy()
-    assert np.all(np.abs(yg[:, :Cout] - U.silu(z)) <= 2 ** -7 * np.abs(U.silu(z)) + 1e-4)
-    assert np.all(yg[:, Cout:] == 7.0)
+    yi = interior(yg)[..., :Cout]
+    assert np.all(np.abs(yi - U.silu(z)) <= 2 ** -7 * np.abs(U.silu(z)) + 1e-4)
+    # The halo holds the periodic copies of the written channels; the others are untouched.
+    np.testing.assert_array_equal(yg[..., :Cout], padded(yi))
+    assert np.all(yg[..., Cout:] == 7.0)
 
 
-def test_tconv_forward_shuffle_epilogue():
+def test_tconv_forward_shuffle_epilogue(tma):
     Bn, h, w, Cin, Cout = 2, 8, 16, 64, 32
-    X, Xd = bf(gen.normal(size=(Bn, h, w, Cin)))
+    x = bf16_round(gen.normal(size=(Bn, h, w, Cin)))
+    X, _ = bf(padded(x))
     Wu, Wud = bf(gen.normal(size=(4, Cout, Cin)) / np.sqrt(Cin))
     bias = torch.tensor(gen.normal(size=Cout), dtype=torch.float32, device=dev)
     Mc = Bn * h * w
-    cat = torch.full((Bn * 4 * h * w, 2 * Cout), 3.0, dtype=torch.bfloat16, device=dev)
-    gemm(op(X, S.SUR_OP_DENSE, Cin, rows=Mc), op(Wu.reshape(4 * Cout, Cin), S.SUR_OP_DENSE, Cin, rows=4 * Cout),
-         Mc, 4 * Cout, Cin, epi=S.SUR_EPI_SHUF, bias=bias, y=cat, ldy=2 * Cout, cy0=Cout, shuf=(Cout, h, w))
-    ref = U.tconv2(Xd, Wud, bias.cpu().numpy().astype(np.float64)).reshape(-1, Cout)
+    cat = torch.full((Bn, 2 * h + 2, 2 * w + 2, 2 * Cout), 3.0, dtype=torch.bfloat16, device=dev)
+    gemm(op(X, S.SUR_OP_PIX, Cin, 0, Cin, Mc, h, w), op(Wu.reshape(4 * Cout, Cin), S.SUR_OP_DENSE, Cin, rows=4 * Cout),
+         Mc, 4 * Cout, Cin, epi=S.SUR_EPI_SHUF, bias=bias, y=cat, ldy=2 * Cout, cy0=Cout, shuf=Cout)
+    ref = U.tconv2(x, Wud, bias.cpu().numpy().astype(np.float64))
     cg = cat.float().cpu().numpy()
-    assert np.all(np.abs(cg[:, Cout:] - ref) <= 2 ** -8 * np.abs(ref) + 1e-5)
-    assert np.all(cg[:, :Cout] == 3.0)
+    ci = interior(cg)[..., Cout:]
+    assert np.all(np.abs(ci - ref) <= 2 ** -8 * np.abs(ref) + 1e-5)
+    np.testing.assert_array_equal(cg[..., Cout:], padded(ci))
+    assert np.all(cg[..., :Cout] == 3.0)
 
 
 def test_up_adjoint_gather():
     Bn, h, w, Cin, Cout = 2, 8, 16, 64, 32
-    dcat, dcatd = bf(gen.normal(size=(Bn, 2 * h, 2 * w, 2 * Cout)))
+    dcat, dcatd = bf(gen.normal(size=(Bn, 2 * h + 2, 2 * w + 2, 2 * Cout)))
     Wu, Wud = bf(gen.normal(size=(4, Cout, Cin)))
     WuT = Wu.reshape(4 * Cout, Cin).t().contiguous()
     Mc = Bn * h * w
-    out = torch.full((Mc, Cin), float("nan"), device=dev)
+    out = torch.full((Bn, h + 2, w + 2, Cin), float("nan"), device=dev)
     gemm(op(dcat, S.SUR_OP_UPADJ, 2 * Cout, Cout, Cout, Mc, h, w), op(WuT, S.SUR_OP_DENSE, 4 * Cout, rows=Cin),
          Mc, Cin, 4 * Cout, out=out, ldo=Cin)
-    dy = dcatd[..., Cout:]
-    ref = U.tconv2_bwd(np.zeros((Bn, h, w, Cin)), dy, Wud)[0].reshape(Mc, Cin)
-    absref = U.tconv2_bwd(np.zeros((Bn, h, w, Cin)), np.abs(dy), np.abs(Wud))[0].reshape(Mc, Cin)
-    close(out.cpu().numpy(), ref, absref)
+    dy = interior(dcatd)[..., Cout:]
+    ref = U.tconv2_bwd(np.zeros((Bn, h, w, Cin)), dy, Wud)[0]
+    absref = U.tconv2_bwd(np.zeros((Bn, h, w, Cin)), np.abs(dy), np.abs(Wud))[0]
+    close(interior(out.cpu().numpy()), ref, absref)
 
 
 @pytest.mark.parametrize("Cin,Cout,splits", [(64, 32, 4), (8, 32, 3), (128, 256, 2)])
 def test_conv_weight_gradient_mn_major_split_k(Cin, Cout, splits):
     Bn, H, W = 2, 16, 32
-    X, Xd = bf(gen.normal(size=(Bn, H, W, Cin)))
-    dZ, dZd = bf(gen.normal(size=(Bn, H, W, Cout)))
+    x = bf16_round(gen.normal(size=(Bn, H, W, Cin)))
+    X, _ = bf(padded(x))
+    dZ, dZd = bf(gen.normal(size=(Bn, H + 2, W + 2, Cout)))
     kp = U.kp_of(Cin)
     M = Bn * H * W
     out = torch.zeros(kp, Cout, device=dev)
-    gemm(op(X, S.SUR_OP_TCONV3, Cin, 0, Cin, 9 * Cin, H, W), op(dZ, S.SUR_OP_TDENSE, Cout, rows=Cout),
+    gemm(op(X, S.SUR_OP_TCONV3, Cin, 0, Cin, 9 * Cin, H, W), op(dZ, S.SUR_OP_TPIX, Cout, 0, 0, Cout, H, W),
          kp, Cout, M, epi=S.SUR_EPI_F32_ATOMIC, out=out, ldo=Cout, splits=splits)
-    ref = U.conv3_bwd_weight(Xd, dZd)[0].reshape(9 * Cin, Cout)
-    absref = U.conv3_bwd_weight(np.abs(Xd), np.abs(dZd))[0].reshape(9 * Cin, Cout)
+    dz = interior(dZd)
+    ref = U.conv3_bwd_weight(x, dz)[0].reshape(9 * Cin, Cout)
+    absref = U.conv3_bwd_weight(np.abs(x), np.abs(dz))[0].reshape(9 * Cin, Cout)
     g = out.cpu().numpy()
     close(g[:9 * Cin], ref, absref)
     assert np.all(g[9 * Cin:] == 0)
@@ -161,15 +193,16 @@ def test_conv_weight_gradient_mn_major_split_k(Cin, Cout, splits):
 
 def test_tconv_weight_gradient_mn_major():
     Bn, h, w, Cin, Cout = 2, 8, 16, 64, 32
-    X, Xd = bf(gen.normal(size=(Bn, h, w, Cin)))
-    dcat, dcatd = bf(gen.normal(size=(Bn, 2 * h, 2 * w, 2 * Cout)))
+    X, Xd = bf(gen.normal(size=(Bn, h + 2, w + 2, Cin)))
+    dcat, dcatd = bf(gen.normal(size=(Bn, 2 * h + 2, 2 * w + 2, 2 * Cout)))
     Mc = Bn * h * w
     out = torch.zeros(4 * Cout, Cin, device=dev)
-    gemm(op(dcat, S.SUR_OP_TUP, 2 * Cout, Cout, Cout, 4 * Cout, h, w), op(X, S.SUR_OP_TDENSE, Cin, rows=Cin),
+    gemm(op(dcat, S.SUR_OP_TUP, 2 * Cout, Cout, Cout, 4 * Cout, h, w), op(X, S.SUR_OP_TPIX, Cin, 0, 0, Cin, h, w),
          4 * Cout, Cin, Mc, epi=S.SUR_EPI_F32_ATOMIC, out=out, ldo=Cin, splits=2)
-    dy = dcatd[..., Cout:]
-    ref = U.tconv2_bwd(Xd, dy, np.zeros((4, Cout, Cin)))[1].reshape(4 * Cout, Cin)
-    absref = U.tconv2_bwd(np.abs(Xd), np.abs(dy), np.zeros((4, Cout, Cin)))[1].reshape(4 * Cout, Cin)
+    dy = interior(dcatd)[..., Cout:]
+    xi = interior(Xd)
+    ref = U.tconv2_bwd(xi, dy, np.zeros((4, Cout, Cin)))[1].reshape(4 * Cout, Cin)
+    absref = U.tconv2_bwd(np.abs(xi), np.abs(dy), np.zeros((4, Cout, Cin)))[1].reshape(4 * Cout, Cin)
     close(out.cpu().numpy(), ref, absref)
 
 
@@ -224,15 +257,11 @@ def smooth_fields(Bn, H, W, seed):
     return x, y
 
 
-def bf16_round(a):
-    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
-
-
 def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def test_network_forward_backward_against_oracle():
+def test_network_forward_backward_against_oracle(tma):
     Bn, H, W = 2, 16, 32
     x, y = smooth_fields(Bn, H, W, 3)
     with S.Surrogate(H, W, seed=5) as m:
