@@ -416,6 +416,7 @@ __global__ void __launch_bounds__(160, 1) k_gemm_cpasync(const KArgs g)
 // ---------------------------------------------------------------------------
 struct TArgs {
     int nkb;
+    int mtiles, ntiles;   // tile grid (the launch grid is smaller: CTAs loop over tiles)
     int kind;          // SUR_OP_CONV3 or SUR_OP_PIX
     int lc, c0;        // log2 channels of the gathered tensor, first channel
     int lh, lw;        // interior grid of A
@@ -451,8 +452,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// ASW: inner width of one A box in bytes (128: 64 channels, swizzle 128 B;
-// 64: 32 channels, swizzle 64 B; 16: 8 channels, no swizzle).
+// Persistent TMA GEMM.  ASW: inner width of one A box in bytes (128: 64
+// channels, swizzle 128 B; 64: 32 channels, swizzle 64 B; 16: 8 channels, no
+// swizzle).  Each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... with
+// two TMEM accumulators, so the epilogue of one tile overlaps the mainloop of
+// the next.
+//   warp 4 (one thread): TMA producer        full[s]   <- expect_tx + TMA bytes
+//   warp 5 (one thread): MMA issuer          empty[s]  <- tcgen05.commit
+//   warps 0-3: epilogue                      tfull[b]  <- tcgen05.commit (accumulator b ready)
+//                                            tempty[b] <- 128 epilogue arrivals (b drained)
 template <int BN, int ASW>
 __global__ void __launch_bounds__(192, 1)
     k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TArgs g)
@@ -462,20 +470,24 @@ __global__ void __launch_bounds__(192, 1)
     constexpr int CB = ASW / 2;               // channels per box
     constexpr int NBOX = 64 / CB;             // A boxes per K block
     constexpr int BOXB = BM * ASW;            // bytes per A box
+    constexpr int TCOLS = 2 * BN < 32 ? 32 : 2 * BN;
     extern __shared__ unsigned char dsm_raw[];
-    __shared__ __align__(8) uint64_t full[NS], empty[NS], done_bar;
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[2], tempty[2], done_bar;
     __shared__ uint32_t tmem_sh;
     __shared__ int abort_flag;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const long long m0 = (long long)blockIdx.x * BM;
-    const int n0 = blockIdx.y * BN;
     volatile int *abort_v = &abort_flag;
+    const int ntiles = g.mtiles * g.ntiles;
 
-    if (warp == 0) tmem_alloc(&tmem_sh, Tmem<BN>::COLS);
+    if (warp == 0) tmem_alloc(&tmem_sh, TCOLS);
     if (t == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull[b]), 1);
+            mbar_init(smem_u32(&tempty[b]), 128);
         }
         mbar_init(smem_u32(&done_bar), 1);
         abort_flag = 0;
@@ -493,70 +505,103 @@ __global__ void __launch_bounds__(192, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
             const int H = 1 << g.lh, W = 1 << g.lw;
-            const int b0 = (int)(m0 >> (g.lh + g.lw));
-            const int y0 = (int)((m0 >> g.lw) & (H - 1)), x0 = (int)(m0 & (W - 1));
-            for (int kb = 0; kb < g.nkb; ++kb) {
-                const int s = kb % NS;
-                if (kb >= NS && !mbar_wait(smem_u32(&empty[s]), ((kb / NS) - 1) & 1, abort_v)) {
-                    *abort_v = 1;
-                    break;
-                }
-                const uint32_t sa = sbase + (uint32_t)(s * Cf::STAGE);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
-                             "r"((uint32_t)Cf::STAGE));
-#pragma unroll
-                for (int j = 0; j < NBOX; ++j) {
-                    const int k = kb * 64 + j * CB;              // first K index of the box
-                    int tap = 4, cc = k;                         // PIX: centre tap, channels k..
-                    if (g.kind == SUR_OP_CONV3) {
-                        tap = k >> g.lc;
-                        cc = k & ((1 << g.lc) - 1);
+            long long it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const long long m0 = (long long)(tile / g.ntiles) * BM;
+                const int n0 = (tile % g.ntiles) * BN;
+                const int b0 = (int)(m0 >> (g.lh + g.lw));
+                const int y0 = (int)((m0 >> g.lw) & (H - 1)), x0 = (int)(m0 & (W - 1));
+                for (int kb = 0; kb < g.nkb; ++kb, ++it) {
+                    const int s = (int)(it % NS);
+                    if (it >= NS && !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((it / NS) - 1) & 1), abort_v)) {
+                        *abort_v = 1;
+                        ok = false;
+                        break;
                     }
-                    const int dy = ((tap * 11) >> 5) - 1, dx = tap - 3 * (dy + 1) - 1;
-                    // Taps 9.. (K padding) load a box wholly below the tensor: zeros.
-                    const int yc = tap < 9 ? y0 + 1 + dy : H + 2;
-                    tma_load_4d(sa + j * BOXB, &tmA, g.c0 + cc, x0 + 1 + dx, yc, b0, smem_u32(&full[s]));
+                    const uint32_t sa = sbase + (uint32_t)(s * Cf::STAGE);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
+                                 "r"((uint32_t)Cf::STAGE));
+#pragma unroll
+                    for (int j = 0; j < NBOX; ++j) {
+                        const int k = kb * 64 + j * CB;          // first K index of the box
+                        int tap = 4, cc = k;                     // PIX: centre tap, channels k..
+                        if (g.kind == SUR_OP_CONV3) {
+                            tap = k >> g.lc;
+                            cc = k & ((1 << g.lc) - 1);
+                        }
+                        const int dy = ((tap * 11) >> 5) - 1, dx = tap - 3 * (dy + 1) - 1;
+                        // Taps 9.. (K padding) load a box wholly below the tensor: zeros.
+                        const int yc = tap < 9 ? y0 + 1 + dy : H + 2;
+                        tma_load_4d(sa + j * BOXB, &tmA, g.c0 + cc, x0 + 1 + dx, yc, b0, smem_u32(&full[s]));
+                    }
+                    tma_load_2d(sa + Cf::A_BYTES, &tmB, g.b_c0 + kb * 64, n0, smem_u32(&full[s]));
                 }
-                tma_load_2d(sa + Cf::A_BYTES, &tmB, g.b_c0 + kb * 64, n0, smem_u32(&full[s]));
             }
         }
     } else if (warp == 5) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             const uint32_t idesc = make_idesc(BN, false, false);
-            for (int kb = 0; kb < g.nkb; ++kb) {
-                const int s = kb % NS;
-                if (!mbar_wait(smem_u32(&full[s]), (kb / NS) & 1, abort_v)) {
+            long long it = 0;
+            int lt = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+                const int buf = lt & 1;
+                if (lt >= 2 && !mbar_wait(smem_u32(&tempty[buf]), (uint32_t)(((lt >> 1) - 1) & 1), abort_v)) {
                     *abort_v = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t sa = sbase + (uint32_t)(s * Cf::STAGE), sb = sa + Cf::A_BYTES;
+                const uint32_t acc_t = tmem + (uint32_t)(buf * BN);
+                for (int kb = 0; kb < g.nkb; ++kb, ++it) {
+                    const int s = (int)(it % NS);
+                    if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((it / NS) & 1), abort_v)) {
+                        *abort_v = 1;
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t sa = sbase + (uint32_t)(s * Cf::STAGE), sb = sa + Cf::A_BYTES;
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k) {
-                    uint64_t da;
-                    if (ASW == 128) da = smem_desc(sa + k * 32, 16, 1024, 2);
-                    else if (ASW == 64) da = smem_desc(sa + (k >> 1) * BOXB + (k & 1) * 32, 16, 512, 4);
-                    else da = smem_desc(sa + k * 2 * BOXB, BOXB, 128, 0);
-                    const uint64_t db = smem_desc(sb + k * 32, 16, 1024, 2);
-                    mma_bf16(tmem, da, db, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < BK / 16; ++k) {
+                        uint64_t da;
+                        if (ASW == 128) da = smem_desc(sa + k * 32, 16, 1024, 2);
+                        else if (ASW == 64) da = smem_desc(sa + (k >> 1) * BOXB + (k & 1) * 32, 16, 512, 4);
+                        else da = smem_desc(sa + k * 2 * BOXB, BOXB, 128, 0);
+                        const uint64_t db = smem_desc(sb + k * 32, 16, 1024, 2);
+                        mma_bf16(acc_t, da, db, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    }
+                    mma_commit(smem_u32(&empty[s]));
                 }
-                mma_commit(smem_u32(&empty[s]));
+                if (ok) mma_commit(smem_u32(&tfull[buf]));
             }
-            mma_commit(smem_u32(&done_bar));
+            mma_commit(smem_u32(&done_bar));   // arrives once every MMA above completed
         }
     } else {
         // ---------------- epilogue (warps 0-3) ----------------
-        const bool fin = mbar_wait(smem_u32(&done_bar), 0);
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (!fin) *abort_v = 1;
-        __syncwarp();
-        if (__all_sync(0xffffffffu, fin && !*abort_v && g.nkb > 0)) epilogue<BN>(g.e, tmem, m0, n0, warp, lane);
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            const bool ready = mbar_wait(smem_u32(&tfull[buf]), (uint32_t)((lt >> 1) & 1), abort_v);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (!__all_sync(0xffffffffu, ready && !*abort_v)) {
+                *abort_v = 1;
+                break;
+            }
+            const long long m0 = (long long)(tile / g.ntiles) * BM;
+            const int n0 = (tile % g.ntiles) * BN;
+            epilogue<BN>(g.e, tmem + (uint32_t)(buf * BN), m0, n0, warp, lane);
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])));
+        }
+        // Tensor memory must be idle before it is freed.
+        if (!mbar_wait(smem_u32(&done_bar), 0)) *abort_v = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (t == 0 && *abort_v) atomicExch(g.e.status, 1);
-    if (warp == 0) tmem_free(tmem, Tmem<BN>::COLS);
+    if (warp == 0) tmem_free(tmem, TCOLS);
 }
 
 }  // namespace
@@ -646,11 +691,20 @@ template <int BN, int ASW>
 cudaError_t launch_tma(const CUtensorMap &ma, const CUtensorMap &mb, const TArgs &g, long long mtiles,
                        cudaStream_t st)
 {
-    static int attr_dev = -1;
+    static int attr_dev = -1, sms = 0;
     cudaError_t e = set_smem(k_gemm_tma<BN, ASW>, CfgT<BN>::SMEM, attr_dev);
     if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)mtiles, (unsigned)(g.e.N / BN));
-    k_gemm_tma<BN, ASW><<<grid, 192, CfgT<BN>::SMEM, st>>>(ma, mb, g);
+    if (!sms) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    }
+    TArgs gg = g;
+    gg.mtiles = (int)mtiles;
+    gg.ntiles = g.e.N / BN;
+    const long long tiles = (long long)gg.mtiles * gg.ntiles;
+    const long long ctas = tiles < 2LL * sms ? tiles : 2LL * sms;   // two resident CTAs per SM
+    k_gemm_tma<BN, ASW><<<(unsigned)ctas, 192, CfgT<BN>::SMEM, st>>>(ma, mb, gg);
     return cudaGetLastError();
 }
 
