@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-enum { SUR_OK = 0, SUR_EINVAL = 1, SUR_ECUDA = 2, SUR_ENOMEM = 3, SUR_ETIMEOUT = 4 };
+enum { SUR_OK = 0, SUR_EINVAL = 1, SUR_ECUDA = 2, SUR_ENOMEM = 3, SUR_ETIMEOUT = 4, SUR_EUNPHYSICAL = 5 };
 
 /* ---------------------------------------------------------------------------
  * Layer primitives (exposed for testing and for callers that build their own
@@ -166,22 +166,28 @@ int sur_infer(sur_model *m, const float *d_x, float *d_y, int batch);
 int sur_indicators(const float *d_fields, int batch, int H, int W, float rho_mid, double *d_out, void *stream);
 
 /* Rollout of `windows` windows of `steps` lattice steps each on the fields
- * d_fields (in/out).  Each window the surrogate proposes the next state; if for
- * any domain the mass differs from the mass at the start of the rollout by more
- * than max_mass_drift (relative), the liquid node count (rho > rho_mid) differs
- * from that of the previous window by more than max_area_change (relative), or
- * a field is not finite, the proposal is discarded and the window is advanced
- * by the lattice Boltzmann context lb instead (nz = batch layers of H x W,
- * D2Q9, not FP64).  The first fallback window and every fallback window that
- * follows an accepted surrogate window restart lb from the local equilibrium of
- * the current fields (lbm_reset_device); consecutive fallback windows continue
- * the lattice Boltzmann state, so a rollout in which every window falls back is
- * exactly a plain lattice Boltzmann run from the equilibrium of the start fields.
- * h_used_lb (host, windows entries, may be NULL) records 1 for such windows;
- * *n_fallback (host) counts them.  Synchronises once per window. */
+ * d_fields (in/out).  Each window the surrogate proposes the next state.  With
+ * project_mass != 0 the proposal's density is shifted per domain so that each
+ * domain keeps the mass it had at the start of the rollout (the lattice
+ * Boltzmann step conserves mass exactly).  The proposal is discarded if, for
+ * any domain, a field is not finite or rho or T is not positive, the mass
+ * differs from the start by more than max_mass_drift (relative), or the liquid
+ * node count (rho > rho_mid) differs from the previous window's by more than
+ * max_area_change (relative); the window is then advanced by the lattice
+ * Boltzmann context lb instead (nz = batch layers of H x W, D2Q9, not FP64).
+ * The first fallback window and every fallback window that follows an accepted
+ * surrogate window restart lb from the local equilibrium of the current fields
+ * (lbm_reset_device); consecutive fallback windows continue the lattice
+ * Boltzmann state, so a rollout in which every window falls back is exactly a
+ * plain lattice Boltzmann run from the equilibrium of the start fields.
+ * h_used_lb (host, windows entries, may be NULL) records 1 for fallback
+ * windows; *n_fallback (host) counts them.  SUR_EUNPHYSICAL if a lattice
+ * Boltzmann window itself ends non-finite or non-positive (the fields then hold
+ * that state).  Synchronises once or twice per window. */
 typedef struct sur_rollout_cfg {
     int windows, steps;
     float rho_mid, max_mass_drift, max_area_change;
+    int project_mass;
 } sur_rollout_cfg;
 int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur_rollout_cfg *cfg,
                 unsigned char *h_used_lb, int *n_fallback);

@@ -683,16 +683,23 @@ int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur
 {
     if (!m || !lb || !d_fields || !cfg || batch < 1 || cfg->windows < 0 || cfg->steps < 1)
         return fail(m, SUR_EINVAL, "invalid arguments");
+    if (batch > 4096) return fail(m, SUR_EINVAL, "at most 4096 domains per rollout");
     const long long Mb = (long long)m->H * m->W, N = Mb * batch;
     int rc = ensure_batch(m, batch, m->train_buffers);
     if (rc) return rc;
-    if (!m->ind) CK(cudaMalloc(&m->ind, sizeof(double) * 2 * 4096));
-    if (batch > 4096) return fail(m, SUR_EINVAL, "at most 4096 domains per rollout");
+    if (!m->ind) CK(cudaMalloc(&m->ind, sizeof(double) * 2 * 4096 + sizeof(float) * 4096));
+    float *d_delta = reinterpret_cast<float *>(m->ind + 2 * 4096);
     std::vector<double> cur(2 * batch), nxt(2 * batch), mass0(batch);
-    // Indicators of the starting fields.
-    CK(evsur::indicators(d_fields, batch, Mb, cfg->rho_mid, m->ind, m->status + 1, m->stream));
-    CK(cudaMemcpyAsync(cur.data(), m->ind, sizeof(double) * 2 * batch, cudaMemcpyDeviceToHost, m->stream));
-    if ((rc = check_status(m, nullptr))) return rc;
+    std::vector<float> delta(batch);
+    // Indicators of d_fields into host (v); *invalid = the invalid flag.
+    auto measure = [&](const float *F, std::vector<double> &v, int *invalid) -> int {
+        CK(evsur::indicators(F, batch, Mb, cfg->rho_mid, m->ind, m->status + 1, m->stream));
+        CK(cudaMemcpyAsync(v.data(), m->ind, sizeof(double) * 2 * batch, cudaMemcpyDeviceToHost, m->stream));
+        return check_status(m, invalid);
+    };
+    int bad = 0;
+    if ((rc = measure(d_fields, cur, &bad))) return rc;
+    if (bad) return fail(m, SUR_EUNPHYSICAL, "the start fields are not finite and positive");
     for (int b = 0; b < batch; ++b) mass0[b] = cur[2 * b];
     int fallbacks = 0;
     // lb_current: the context's populations are the lattice Boltzmann state of
@@ -701,15 +708,18 @@ int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur
     bool lb_current = false;
     for (int w = 0; w < cfg->windows; ++w) {
         if ((rc = forward(m, d_fields, batch, false))) return rc;
-        CK(evsur::head(m->Y03, N, m->lh, m->lw, m->P + m->head_w, m->P + m->head_b, m->norm, d_fields, nullptr, 1, nullptr,
-                       nullptr, m->next, m->stream));
-        CK(evsur::indicators(m->next, batch, Mb, cfg->rho_mid, m->ind, m->status + 1, m->stream));
-        CK(cudaMemcpyAsync(nxt.data(), m->ind, sizeof(double) * 2 * batch, cudaMemcpyDeviceToHost, m->stream));
-        int nonfinite = 0;
-        if ((rc = check_status(m, &nonfinite))) return rc;
-        // Acceptance: cumulative mass drift against the start, liquid-count change
-        // against the previous window, all fields finite.
-        bool accept = !nonfinite;
+        CK(evsur::head(m->Y03, N, m->lh, m->lw, m->P + m->head_w, m->P + m->head_b, m->norm, d_fields, nullptr, 1,
+                       nullptr, nullptr, m->next, m->stream));
+        if ((rc = measure(m->next, nxt, &bad))) return rc;
+        if (cfg->project_mass && !bad) {
+            for (int b = 0; b < batch; ++b) delta[b] = (float)((nxt[2 * b] - mass0[b]) / (double)Mb);
+            CK(cudaMemcpyAsync(d_delta, delta.data(), sizeof(float) * batch, cudaMemcpyHostToDevice, m->stream));
+            CK(evsur::shift_rho(m->next, batch, Mb, d_delta, m->stream));
+            if ((rc = measure(m->next, nxt, &bad))) return rc;
+        }
+        // Acceptance: finite and positive fields, cumulative mass drift against the
+        // start, liquid-count change against the previous window.
+        bool accept = !bad;
         for (int b = 0; b < batch && accept; ++b) {
             const double dm = fabs(nxt[2 * b] - mass0[b]) / fabs(mass0[b]);
             const double da = fabs(nxt[2 * b + 1] - cur[2 * b + 1]) / fmax(cur[2 * b + 1], 1.0);
@@ -728,9 +738,12 @@ int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur
             if (lrc == LBM_OK) lrc = lbm_moments_device(lb, d_fields, d_fields + N, d_fields + 3 * N);
             if (lrc == LBM_OK) lrc = lbm_sync(lb);
             if (lrc != LBM_OK) return fail(m, SUR_ECUDA, "fallback lattice Boltzmann window: %s", lbm_last_error(lb));
-            CK(evsur::indicators(d_fields, batch, Mb, cfg->rho_mid, m->ind, m->status + 1, m->stream));
-            CK(cudaMemcpyAsync(cur.data(), m->ind, sizeof(double) * 2 * batch, cudaMemcpyDeviceToHost, m->stream));
-            if ((rc = check_status(m, nullptr))) return rc;
+            if ((rc = measure(d_fields, cur, &bad))) return rc;
+            if (bad) {
+                if (h_used_lb) h_used_lb[w] = 1;
+                if (n_fallback) *n_fallback = fallbacks + 1;
+                return fail(m, SUR_EUNPHYSICAL, "lattice Boltzmann window %d ended non-finite or non-positive", w);
+            }
             lb_current = true;
             ++fallbacks;
         }

@@ -268,9 +268,9 @@ __global__ void k_up_weights(const float *Wm, int Cin, int Cout, bf16 *Wb, bf16 
     }
 }
 
-// Per-domain FP64 sums of rho and of the liquid count (rho > rho_mid), plus a
-// non-finite flag over all four fields: out[2b], out[2b+1]; nonfinite[0] |= 1.
-__global__ void k_indicators(const float *F, long long M, long long Mb, float rho_mid, double *out, int *nonfinite)
+// Per-domain FP64 sums of rho and of the liquid count (rho > rho_mid): out[2b],
+// out[2b+1]; invalid[0] |= 1 if any field is not finite or rho or T is not > 0.
+__global__ void k_indicators(const float *F, long long M, long long Mb, float rho_mid, double *out, int *invalid)
 {
     __shared__ double s1[256], s2[256];
     const long long b = blockIdx.y;
@@ -281,10 +281,12 @@ __global__ void k_indicators(const float *F, long long M, long long Mb, float rh
         const float r = F[n];
         a1 += r;
         a2 += r > rho_mid ? 1.0 : 0.0;
-        if (nonfinite)
+        if (invalid) {
             for (int c = 0; c < 4; ++c) bad |= !isfinite(F[c * M + n]);
+            bad |= !(r > 0.f) || !(F[3 * M + n] > 0.f);
+        }
     }
-    if (bad) atomicOr(nonfinite, 1);
+    if (bad) atomicOr(invalid, 1);
     s1[threadIdx.x] = a1;
     s2[threadIdx.x] = a2;
     __syncthreads();
@@ -301,7 +303,25 @@ __global__ void k_indicators(const float *F, long long M, long long Mb, float rh
     }
 }
 
+// rho[b*Mb + i] -= delta[b]: restores each domain's mass (the lattice Boltzmann
+// step conserves it exactly).
+__global__ void k_shift_rho(float *rho, long long Mb, const float *delta)
+{
+    const long long b = blockIdx.y;
+    const float d = delta[b];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Mb; i += (long long)gridDim.x * blockDim.x)
+        rho[b * Mb + i] -= d;
+}
+
 }  // namespace
+
+cudaError_t shift_rho(float *rho, int batch, long long Mb, const float *delta, cudaStream_t st)
+{
+    long long gx = (Mb + 255) / 256;
+    if (gx > 64) gx = 64;
+    k_shift_rho<<<dim3((unsigned)gx, (unsigned)batch), 256, 0, st>>>(rho, Mb, delta);
+    return cudaGetLastError();
+}
 
 cudaError_t silu_bwd(const bf16 *dY, int ldd, const bf16 *Z, long long M, int lh, int lw, int C, bf16 *dZ,
                      cudaStream_t st)
@@ -372,7 +392,7 @@ cudaError_t up_weights(const float *Wm, int Cin, int Cout, bf16 *Wb, bf16 *Wt, c
     return cudaGetLastError();
 }
 
-cudaError_t indicators(const float *F, int batch, long long Mb, float rho_mid, double *out, int *nonfinite,
+cudaError_t indicators(const float *F, int batch, long long Mb, float rho_mid, double *out, int *invalid,
                        cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * 2 * batch, st);
@@ -380,7 +400,7 @@ cudaError_t indicators(const float *F, int batch, long long Mb, float rho_mid, d
     long long gx = (Mb + 255) / 256;
     if (gx > 64) gx = 64;
     const dim3 grid((unsigned)gx, (unsigned)batch);
-    k_indicators<<<grid, 256, 0, st>>>(F, (long long)batch * Mb, Mb, rho_mid, out, nonfinite);
+    k_indicators<<<grid, 256, 0, st>>>(F, (long long)batch * Mb, Mb, rho_mid, out, invalid);
     return cudaGetLastError();
 }
 

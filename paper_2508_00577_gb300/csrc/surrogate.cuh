@@ -87,7 +87,8 @@ cudaError_t adam(float *w, const float *g, float *m, float *v, long long n, floa
                  float c1, float c2, cudaStream_t st);
 cudaError_t conv_weights(const float *Wt, int Cin, int Cout, int Kp, int Kpo, bf16 *Wb, bf16 *Wf, cudaStream_t st);
 cudaError_t up_weights(const float *Wm, int Cin, int Cout, bf16 *Wb, bf16 *Wt, cudaStream_t st);
-cudaError_t indicators(const float *F, int batch, long long Mb, float rho_mid, double *out, int *nonfinite,
+cudaError_t indicators(const float *F, int batch, long long Mb, float rho_mid, double *out, int *invalid,
                        cudaStream_t st);
+cudaError_t shift_rho(float *rho, int batch, long long Mb, const float *delta, cudaStream_t st);
 
 }  // namespace evsur

@@ -14,12 +14,12 @@ import numpy as np
 
 from . import lib as _lib_loader
 
-SUR_OK, SUR_EINVAL, SUR_ECUDA, SUR_ENOMEM, SUR_ETIMEOUT = 0, 1, 2, 3, 4
+SUR_OK, SUR_EINVAL, SUR_ECUDA, SUR_ENOMEM, SUR_ETIMEOUT, SUR_EUNPHYSICAL = 0, 1, 2, 3, 4, 5
 SUR_OP_DENSE, SUR_OP_PIX, SUR_OP_CONV3, SUR_OP_UPADJ, SUR_OP_TPIX, SUR_OP_TCONV3, SUR_OP_TUP = range(7)
 SUR_EPI_BF16, SUR_EPI_F32, SUR_EPI_F32_ATOMIC, SUR_EPI_CONV, SUR_EPI_SHUF = range(5)
 
 _ERRNAMES = {SUR_EINVAL: "SUR_EINVAL", SUR_ECUDA: "SUR_ECUDA", SUR_ENOMEM: "SUR_ENOMEM",
-             SUR_ETIMEOUT: "SUR_ETIMEOUT"}
+             SUR_ETIMEOUT: "SUR_ETIMEOUT", SUR_EUNPHYSICAL: "SUR_EUNPHYSICAL"}
 
 # Every symbol include/evsur.h declares.
 EXPORTED_SYMBOLS = (
@@ -56,7 +56,8 @@ class sur_gemm_args(ctypes.Structure):
 
 class sur_rollout_cfg(ctypes.Structure):
     _fields_ = [("windows", ctypes.c_int), ("steps", ctypes.c_int), ("rho_mid", ctypes.c_float),
-                ("max_mass_drift", ctypes.c_float), ("max_area_change", ctypes.c_float)]
+                ("max_mass_drift", ctypes.c_float), ("max_area_change", ctypes.c_float),
+                ("project_mass", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -166,8 +167,9 @@ def sur_indicators(d_fields, batch, H, W, rho_mid, d_out, stream=0):
     _check(lib().sur_indicators(d_fields, batch, H, W, rho_mid, d_out, stream))
 
 
-def sur_rollout(model, lb_ctx, d_fields, batch, windows, steps, rho_mid, max_mass_drift, max_area_change):
-    cfg = sur_rollout_cfg(windows, steps, rho_mid, max_mass_drift, max_area_change)
+def sur_rollout(model, lb_ctx, d_fields, batch, windows, steps, rho_mid, max_mass_drift, max_area_change,
+                project_mass=False):
+    cfg = sur_rollout_cfg(windows, steps, rho_mid, max_mass_drift, max_area_change, 1 if project_mass else 0)
     used = (ctypes.c_ubyte * max(windows, 1))()
     nfb = ctypes.c_int(0)
     _check(lib().sur_rollout(model, lb_ctx, d_fields, batch, ctypes.byref(cfg), used, ctypes.byref(nfb)), model)
@@ -233,8 +235,10 @@ class Surrogate:
     def infer(self, d_x, d_y, batch):
         sur_infer(self.m, d_x, d_y, batch)
 
-    def rollout(self, lb_ctx, d_fields, batch, windows, steps, rho_mid, max_mass_drift=1e-3, max_area_change=0.02):
-        return sur_rollout(self.m, lb_ctx, d_fields, batch, windows, steps, rho_mid, max_mass_drift, max_area_change)
+    def rollout(self, lb_ctx, d_fields, batch, windows, steps, rho_mid, max_mass_drift=1e-3, max_area_change=0.02,
+                project_mass=False):
+        return sur_rollout(self.m, lb_ctx, d_fields, batch, windows, steps, rho_mid, max_mass_drift, max_area_change,
+                           project_mass)
 
     def close(self):
         if self.m:
