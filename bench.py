@@ -508,6 +508,59 @@ def run_surrogate(args):
     return 0
 
 
+def run_surrogate_kernels(args):
+    """Kernel-level timing of the surrogate on batch --batch of 256^2 domains: two
+    inferences and one training step (the case the ncu summaries capture), then
+    CUDA-event timing of each over --steps repetitions."""
+    import torch
+
+    from paper_2508_00577_gb300 import surrogate as S
+
+    dev = "cuda"
+    bs, n = args.batch, SUR_N
+    r = np.random.default_rng(0)
+    yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    base = np.stack([np.sin(2 * np.pi * (k + 1) * yy / n + k) * np.cos(2 * np.pi * xx / n) for k in range(4)])
+    x = np.concatenate([base.reshape(4, -1)] * bs, axis=1) * np.array([[0.05], [0.004], [0.004], [0.0005]])
+    x += np.array([[0.1], [0.0], [0.0], [0.0075]]) + 1e-4 * r.standard_normal(x.shape)
+    dx = torch.tensor(x, dtype=torch.float32, device=dev).contiguous()
+    dy = dx + 1e-4
+    out = torch.empty_like(dx)
+    m = S.Surrogate(n, n, seed=3)
+    m.set_norm([0.1, 0, 0, 0.0075], [0.05, 0.004, 0.004, 0.0005], [0.002, 0.001, 0.001, 8e-5])
+    torch.cuda.synchronize()
+    for _ in range(2):
+        m.infer(dx.data_ptr(), out.data_ptr(), bs)
+    m.train_step(dx.data_ptr(), dy.data_ptr(), bs, 1e-4, want_loss=False)
+    torch.cuda.synchronize()
+    res = {}
+    for name, fn in (("infer", lambda: m.infer(dx.data_ptr(), out.data_ptr(), bs)),
+                     ("train_step", lambda: m.train_step(dx.data_ptr(), dy.data_ptr(), bs, 1e-4, want_loss=False))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fn()
+        torch.cuda.synchronize()
+        res[name] = (time.perf_counter() - t0) / args.steps * 1e3
+    m.close()
+    flops = 17.93e9 * bs
+    print(json.dumps({"metric": "surrogate inference TFLOP/s", "value": flops / res["infer"] / 1e9, "unit": "TFLOP/s",
+                      "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+                      "config": {"workload": f"U-Net on {bs} x {n}^2 domains", "batch": bs},
+                      "ms_per_inference": res["infer"], "ms_per_train_step": res["train_step"],
+                      "train_tflops": 3 * flops / res["train_step"] / 1e9,
+                      "bf16_peak_tflops": peaks_bf16()}), flush=True)
+    return 0
+
+
+def peaks_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -518,7 +571,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed launch shape W,H of the fused kernel")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate", "surrogate_kernels"],
                     help="sweep: the headline droplet Laplace sweep; ensemble: 512 uneven domains; "
                          "surrogate: U-Net surrogate with lattice Boltzmann fallback vs plain LB")
     ap.add_argument("--domains", type=int, default=None, help="ensemble: 512; surrogate: 32 held-out domains")
@@ -537,6 +590,8 @@ def main():
     if args.workload == "surrogate":
         args.domains = args.domains or 32
         return run_surrogate(args)
+    if args.workload == "surrogate_kernels":
+        return run_surrogate_kernels(args)
     return run(args)
 
 
