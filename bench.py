@@ -126,6 +126,24 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(value, device=None):
+    """The maximum of a per-rank number over all ranks (the job's time is the
+    slowest rank's); the value itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, nodes_per_rank, steps, total_ms):
+    """Whole-job throughput of `world` replicas, each updating nodes_per_rank nodes
+    per step, timed by the slowest rank."""
+    return world * nodes_per_rank * steps / (total_ms * 1e-3) / 1e6
+
+
 def cpu_baseline(steps=None, budget_s=15.0):
     """The FP64 oracle on one 1024^2 layer of the workload (T/Tc = 0.8, R = 128)."""
     import oracle
@@ -224,13 +242,9 @@ def run(args):
     if world > 1:
         torch.distributed.barrier()
     per_step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(per_step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(per_step_ms), dev)
     ms_per_step = total_ms / args.steps
-    value = world * N * args.steps / (total_ms * 1e-3) / 1e6
+    value = job_mlups(world, N, args.steps, total_ms)
 
     ok = np.isfinite(lat.conserved()).all()
     lat.close()
