@@ -530,6 +530,54 @@ def run_surrogate(args):
     return line
 
 
+def run_spinodal3d(args):
+    """3-D spinodal decomposition, 256^3 D3Q27 thermal: mean density at the midpoint of
+    the spinodal region at T/Tc = 0.85 with seeded uniform +-1 % noise, u = 0; FP32
+    storage and arithmetic, and FP16 / BF16 deviation storage with FP32 arithmetic.
+    One line with MLUPS and the fraction of the HBM roofline per storage type
+    (algorithmic bytes: 2 populations x 27 x read + write x storage bytes)."""
+    import torch
+
+    import oracle.eos as E
+    import paper_2508_00577_gb300 as ev
+    from paper_2508_00577_gb300 import inputs
+
+    n = args.n3d
+    _, Tc = ev.lbm_critical_point(1, A, B)
+    RT = 0.85 * Tc
+    s1, s2 = E.spinodal(E.CS, A, B, RT)
+    kappa = E.kappa_for_width(E.CS, A, B, RT, 4.0)
+    rho, u, T = inputs.spinodal_noise(n, n, n, 0.5 * (s1 + s2), RT, amplitude=0.01)
+    peak, peak_kind = peaks()
+    out = {}
+    for prec, name, sb in ((ev.LBM_FP32, "fp32", 4), (ev.LBM_FP16_DEV, "fp16", 2), (ev.LBM_BF16_DEV, "bf16", 2)):
+        p = ev.lbm_params.make(lattice=ev.LBM_D3Q27, nx=n, ny=n, nz=n, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=kappa,
+                               tau=TAU, precision=prec)
+        stream = torch.cuda.Stream()
+        with ev.Lattice(p, rho, u, T, stream=stream.cuda_stream) as g:
+            g.step(args.warmup)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            g.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            launches = ev.lbm_launches_per_step(g.ctx)
+            finite = bool(np.isfinite(g.conserved()).all())
+        bpl = 2 * 27 * 2 * sb
+        out[name] = {"mlups": p.N / (ms * 1e-3) / 1e6, "ms_per_step": ms, "launches_per_step": launches,
+                     "algorithmic_bytes_per_lu": bpl, "achieved_gbs": bpl * p.N / (ms * 1e-3) / 1e9,
+                     "frac": bpl * p.N / (ms * 1e-3) / 1e9 / peak, "finite": finite}
+    print(json.dumps({"metric": "MLUPS", "value": out["fp32"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+                      "data": "synthetic",
+                      "config": {"workload": f"3-D spinodal decomposition, {n}^3 D3Q27 thermal, T/Tc = 0.85",
+                                 "peak": f"{peak} GB/s ({peak_kind})"},
+                      "by_storage": out}), flush=True)
+    return 0
+
+
 def run_surrogate_kernels(args):
     """Kernel-level timing of the surrogate on batch --batch of 256^2 domains: two
     inferences and one training step (the case the ncu summaries capture), then
@@ -594,9 +642,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement in the default run")
     ap.add_argument("--tile", default="", help="fixed launch shape W,H of the fused kernel")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate", "surrogate_kernels"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate", "surrogate_kernels", "spinodal3d"],
                     help="sweep: the headline droplet Laplace sweep; ensemble: 512 uneven domains; "
                          "surrogate: U-Net surrogate with lattice Boltzmann fallback vs plain LB")
+    ap.add_argument("--n3d", type=int, default=256, help="spinodal3d: cube side")
     ap.add_argument("--domains", type=int, default=None, help="ensemble: 512; surrogate: 32 held-out domains")
     ap.add_argument("--train-domains", type=int, default=64)
     ap.add_argument("--train-steps", type=int, default=4000)
@@ -616,6 +665,8 @@ def main():
         return 0
     if args.workload == "surrogate_kernels":
         return run_surrogate_kernels(args)
+    if args.workload == "spinodal3d":
+        return run_spinodal3d(args)
     return run(args)
 
 

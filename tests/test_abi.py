@@ -112,3 +112,31 @@ def test_coexistence_rejects_supercritical_on_host():
     with pytest.raises(ev.LBMError) as e:
         ev.lbm_coexistence(ev.LBM_EOS_CS, 0.1, 4.0, 1.01 * Tc)
     assert e.value.code == ev.LBM_EINVAL
+
+
+def test_surrogate_rejects_invalid_arguments_on_host():
+    """Invalid sizes and layouts are rejected before any CUDA call (no GPU needed)."""
+    from paper_2508_00577_gb300 import surrogate as S
+    for H, W, base in ((15, 16, 32), (16, 24, 32), (8, 16, 32), (16, 16, 16)):
+        with pytest.raises(S.SurError) as e:
+            S.sur_init(H, W, base)
+        assert e.value.code == S.SUR_EINVAL
+    g = S.sur_gemm_args()
+    g.a = S.sur_operand(16, S.SUR_OP_DENSE, 64, 0, 0, 128, 0, 0)
+    g.b = S.sur_operand(16, S.SUR_OP_DENSE, 64, 0, 0, 48, 0, 0)
+    g.M, g.N, g.K, g.splits, g.epi = 128, 48, 64, 1, S.SUR_EPI_F32      # N not a multiple of 32
+    g.out, g.ldo = 16, 48
+    cases = []
+    c = S.sur_gemm_args(); c.a, c.b, c.M, c.N, c.K, c.splits, c.epi, c.out, c.ldo = g.a, g.b, 128, 48, 64, 1, 1, 16, 48
+    cases.append(c)                                                         # N % 32 != 0
+    c = S.sur_gemm_args(); c.a, c.b, c.M, c.N, c.K, c.splits, c.epi, c.out, c.ldo = g.a, g.b, 128, 32, 64, 2, 1, 16, 32
+    cases.append(c)                                                         # split-K without the atomic epilogue
+    c = S.sur_gemm_args(); c.a, c.b, c.M, c.N, c.K, c.splits, c.epi, c.out, c.ldo = g.a, g.b, 128, 32, 72, 1, 1, 16, 32
+    cases.append(c)                                                         # dense K tail beyond ld
+    bad_c = S.sur_operand(16, S.SUR_OP_CONV3, 64, 0, 24, 128, 16, 8)      # C not a power of two
+    c = S.sur_gemm_args(); c.a, c.b, c.M, c.N, c.K, c.splits, c.epi, c.out, c.ldo = bad_c, g.b, 128, 32, 64, 1, 1, 16, 32
+    cases.append(c)
+    for c in cases:
+        with pytest.raises(S.SurError) as e:
+            S.sur_gemm(c, 16)
+        assert e.value.code == S.SUR_EINVAL
