@@ -289,6 +289,17 @@ def run(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    if world == 1 and not args.no_extra:
+        # The other rows, measured on their own workloads: the batched persistent
+        # ensemble (A11) and the 3-D path with reduced-precision storage (A10).
+        eargs = argparse.Namespace(**vars(args))
+        eargs.domains, eargs.steps, eargs.warmup = 512, 2000, 20
+        e_line = run_ensemble(eargs)
+        line["ensemble"] = {k: e_line[k] for k in ("metric", "value", "unit", "steps", "ms_per_step", "config",
+                                                     "roofline", "finite")}
+        sargs3 = argparse.Namespace(**vars(args))
+        sargs3.steps, sargs3.warmup = 20, 3
+        line["spinodal3d"] = run_spinodal3d(sargs3)
     if world == 1 and not args.no_surrogate:
         # The learned-surrogate row: speedup of surrogate + fallback over the plain
         # LB at <= 1e-2 relative density error (separate workload, see run_surrogate).
@@ -339,7 +350,7 @@ def run_ensemble(args):
     achieved = BYTES_PER_LU * N * args.steps / (ms * 1e-3) / 1e9
     finite = all(np.isfinite(bt.moments(d)[0]).all() for d in (0, len(sizes) // 2, len(sizes) - 1))
     bt.close()
-    print(json.dumps({
+    return {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
@@ -349,8 +360,7 @@ def run_ensemble(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "note": f"{BYTES_PER_LU} algorithmic B/LU; peak {peak_kind}"},
         "clocks": clk.summary(), "gpu_launches": 1, "finite": bool(finite),
-    }), flush=True)
-    return 0
+    }
 
 
 # Surrogate workload (A12): droplet-pair domains of 256^2 drawn like the ensemble's
@@ -569,13 +579,12 @@ def run_spinodal3d(args):
         out[name] = {"mlups": p.N / (ms * 1e-3) / 1e6, "ms_per_step": ms, "launches_per_step": launches,
                      "algorithmic_bytes_per_lu": bpl, "achieved_gbs": bpl * p.N / (ms * 1e-3) / 1e9,
                      "frac": bpl * p.N / (ms * 1e-3) / 1e9 / peak, "finite": finite}
-    print(json.dumps({"metric": "MLUPS", "value": out["fp32"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
-                      "data": "synthetic",
-                      "config": {"workload": f"3-D spinodal decomposition, {n}^3 D3Q27 thermal, T/Tc = 0.85",
-                                 "peak": f"{peak} GB/s ({peak_kind})"},
-                      "by_storage": out}), flush=True)
-    return 0
+    return {"metric": "MLUPS", "value": out["fp32"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"3-D spinodal decomposition, {n}^3 D3Q27 thermal, T/Tc = 0.85",
+                       "peak": f"{peak} GB/s ({peak_kind})"},
+            "by_storage": out}
 
 
 def run_surrogate_kernels(args):
@@ -641,6 +650,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement in the default run")
+    ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and 3-D measurements in the default run")
     ap.add_argument("--tile", default="", help="fixed launch shape W,H of the fused kernel")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate", "surrogate_kernels", "spinodal3d"],
                     help="sweep: the headline droplet Laplace sweep; ensemble: 512 uneven domains; "
@@ -658,7 +668,8 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         args.domains = args.domains or 512
-        return run_ensemble(args)
+        print(json.dumps(run_ensemble(args)), flush=True)
+        return 0
     if args.workload == "surrogate":
         args.domains = args.domains or 32
         print(json.dumps(run_surrogate(args)), flush=True)
@@ -666,7 +677,8 @@ def main():
     if args.workload == "surrogate_kernels":
         return run_surrogate_kernels(args)
     if args.workload == "spinodal3d":
-        return run_spinodal3d(args)
+        print(json.dumps(run_spinodal3d(args)), flush=True)
+        return 0
     return run(args)
 
 
