@@ -259,7 +259,8 @@ int lbm_step(lbm_ctx *c, int n_steps)
     if (!c) return LBM_EINVAL;
     if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps must be >= 0");
     const bool fused = !fp64(c) && evlbm::fused2d_supported(c->P.precision, c->Q, c->K);
-    if (!fused) {
+    const bool fused3 = !fp64(c) && evlbm::fused3d_supported(c->P.precision, c->Q, c->K);
+    if (!fused && !fused3) {
         int rc = ensure_scratch(c);
         if (rc) return rc;
     }
@@ -269,6 +270,8 @@ int lbm_step(lbm_ctx *c, int n_steps)
         if (fused)
             e = evlbm::fused2d_step(c->P.precision, c->K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx], c->RT_iso,
                                     c->stream);
+        else if (fused3)
+            e = evlbm::fused3d_step(c->K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx], c->RT_iso, c->stream);
         else if (fp64(c))
             e = evlbm::ref_step_f64(c->Q, c->K, c->scratch, c->RT_iso, c->f[c->cur], c->g[c->cur], c->f[nx],
                                     c->g[nx], c->stream);
@@ -368,15 +371,24 @@ long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
 int lbm_launches_per_step(const lbm_ctx *c)
 {
     if (!c) return -1;
-    return (!fp64(c) && evlbm::fused2d_supported(c->P.precision, c->Q, c->K)) ? 1 : 4;
+    return (!fp64(c) && (evlbm::fused2d_supported(c->P.precision, c->Q, c->K) ||
+                         evlbm::fused3d_supported(c->P.precision, c->Q, c->K)))
+               ? 1
+               : 4;
 }
 
 int lbm_set_tile(lbm_ctx *c, int tile_w, int tile_h)
 {
     if (!c) return LBM_EINVAL;
     bool ok = tile_w == 0 && tile_h == 0;
-    for (int k = 0; k < evlbm::kFusedWidthCount; ++k) ok = ok || (tile_w == evlbm::kFusedWidths[k] && tile_h >= 1);
-    if (!ok) return fail(c, LBM_EINVAL, "tile_w must be one of 64,96,128,192 and tile_h >= 1 (or both 0)");
+    if (c->Q == 27) {
+        ok = ok || (tile_w == evlbm::kFused3dTile && tile_h >= 1);
+        if (!ok) return fail(c, LBM_EINVAL, "D3Q27: tile_w must be 16 and tile_h (z-chunk) >= 1 (or both 0)");
+    } else {
+        for (int k = 0; k < evlbm::kFusedWidthCount; ++k)
+            ok = ok || (tile_w == evlbm::kFusedWidths[k] && tile_h >= 1);
+        if (!ok) return fail(c, LBM_EINVAL, "tile_w must be one of 64,96,128,192 and tile_h >= 1 (or both 0)");
+    }
     c->K.tile_w = tile_w;
     c->K.tile_h = tile_h;
     return LBM_OK;
@@ -390,11 +402,54 @@ int lbm_get_tile(const lbm_ctx *c, int *tile_w, int *tile_h)
     return LBM_OK;
 }
 
+// z-chunk height of the fused D3Q27 kernel by timed probes on the live state
+// (its output buffer is the spare one, so the state is unchanged).
+static int autotune3d(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
+{
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    const int heights[] = {8, 16, 32, 64, 128, 256};
+    const int nx = c->cur ^ 1;
+    float best = 1e30f;
+    int bh = 0;
+    KParams K = c->K;
+    cudaError_t e = cudaSuccess;
+    for (int hi = 0; hi < 6 && e == cudaSuccess; ++hi) {
+        const int H = heights[hi] < c->P.nz ? heights[hi] : c->P.nz;
+        if (hi > 0 && H == (heights[hi - 1] < c->P.nz ? heights[hi - 1] : c->P.nz)) continue;
+        K.tile_w = evlbm::kFused3dTile;
+        K.tile_h = H;
+        for (int s = 0; s <= probe_steps && e == cudaSuccess; ++s) {
+            if (s == 1) e = cudaEventRecord(e0, c->stream);
+            if (e == cudaSuccess)
+                e = evlbm::fused3d_step(K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx], c->RT_iso, c->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            bh = H;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_autotune");
+    c->K.tile_w = evlbm::kFused3dTile;
+    c->K.tile_h = bh;
+    if (tile_w) *tile_w = evlbm::kFused3dTile;
+    if (tile_h) *tile_h = bh;
+    return LBM_OK;
+}
+
 int lbm_autotune(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
 {
     if (!c || probe_steps < 1) return c ? fail(c, LBM_EINVAL, "probe_steps must be >= 1") : LBM_EINVAL;
     if (tile_w) *tile_w = 0;
     if (tile_h) *tile_h = 0;
+    if (!fp64(c) && evlbm::fused3d_supported(c->P.precision, c->Q, c->K)) return autotune3d(c, probe_steps, tile_w, tile_h);
     if (fp64(c) || !evlbm::fused2d_supported(c->P.precision, c->Q, c->K)) return LBM_OK;
     cudaEvent_t e0, e1;
     CK(c, cudaEventCreate(&e0));

@@ -45,6 +45,12 @@ constexpr int kFusedWidthCount = 4;
 extern const int kFusedWidths[kFusedWidthCount];
 void fused2d_default_tile(const KParams &p, int *W, int *H);
 bool fused2d_supported(int prec, int Q, const KParams &p);
+// Fused single-pass D3Q27 step (FP32, divergence force form); the x-y tile is
+// kFused3dTile x kFused3dTile columns, tile_h is the z-chunk height (0 = default).
+constexpr int kFused3dTile = 16;
+bool fused3d_supported(int prec, int Q, const KParams &p);
+cudaError_t fused3d_step(const KParams &p, const void *f, const void *g, void *fo, void *go, const void *RT_iso,
+                         cudaStream_t st);
 cudaError_t fused2d_step(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
                          const void *RT_iso, cudaStream_t st);
 

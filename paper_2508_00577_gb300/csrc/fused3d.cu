@@ -1,0 +1,454 @@
+// Fused single-pass D3Q27 step of the Enskog-Vlasov lattice Boltzmann model
+// (Karlin & Hosseini, arXiv 2508.00577), FP32 storage and arithmetic: one
+// launch per time step does pull streaming, raw moments, the Enskog-gauge force
+// in divergence (Korteweg-stress) form, the shifted velocity and energy
+// (Eqs. u_shift, T_shift), the EOS and gamma0 (Eq. gamma), the corrections
+// Phi, Phi', q' (Eqs. correction_u/gamma/q), the equilibria (Eqs. feq, f_star,
+// geq, gstar, g_corr) and the collision of Eq. (pre_LBM).
+//
+// Work decomposition (2.5-D z-marching).  A CTA owns a 16 x 16 tile of (x, y)
+// output columns of one z-chunk and walks its planes one per iteration; four
+// stages lag by one plane because the collision needs u and T within radius 1,
+// hence F within radius 1, hence the Korteweg stress within radius 2, hence rho
+// within radius 3:
+//   A: rho, j (plane q)            pulled f           on the tile + 3 halo columns (22 x 22)
+//   B: Korteweg stress (q-1)       rho of q-2..q      on the tile + 2 (20 x 20)
+//   C: F, u, T, EOS (q-2)          stress of q-3..q-1, pulled g   (18 x 18)
+//   D: collide (q-3)               u, T fields of q-4..q-2, populations pulled
+//                                  again (L2 hits: stage A/C read them 3/1 planes ago)
+// Shared fields live in 3-deep plane rings sized to the region that reads them;
+// centre values pass from C to D through a 2-deep per-thread ring.
+#include "dispatch.h"
+
+namespace evlbm {
+
+namespace {
+
+constexpr int TX = 16, TY = 16, NT = TX * TY;     // output columns per CTA, threads per CTA
+constexpr int WA = TX + 6, WB = TX + 4, WC = TX + 2;
+constexpr int SA = WA * WA, SB = WB * WB, SC = WC * WC;
+
+// Shared-memory layout (floats).
+constexpr int O_RHO = 0;                          // [3][SA]
+constexpr int O_J = O_RHO + 3 * SA;               // [3 planes][3 comps][SC]
+constexpr int O_PI = O_J + 9 * SC;                // [3 planes][6 comps][SB]  xx xy xz yy yz zz
+constexpr int O_CF = O_PI + 18 * SB;              // [3 planes][7][SC]  ux uy uz qx qy qz wq
+constexpr int O_CEN = O_CF + 21 * SC;             // [2][7][NT]  rho Fx Fy Fz RT theta0 gamma0
+constexpr int SMEM_FLOATS = O_CEN + 14 * NT;
+constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
+
+struct Args {
+    const float *f, *g;
+    float *fo, *go;
+    const float *RT_iso;
+    int nx, ny, nz, HZ;
+    unsigned N;
+    int eos;
+    float a, b, kappa, lambda, c_eq, c_star;
+};
+
+__device__ __forceinline__ int wrapi(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+constexpr __host__ __device__ int cxi(int i) { return i % 3 - 1; }
+constexpr __host__ __device__ int cyi(int i) { return (i / 3) % 3 - 1; }
+constexpr __host__ __device__ int czi(int i) { return i / 9 - 1; }
+// 1-D weights 2/3 (c = 0), 1/6 (c = +-1); w_i is their product.
+constexpr __host__ __device__ float w1(int c) { return c == 0 ? 2.f / 3.f : 1.f / 6.f; }
+constexpr __host__ __device__ float wi(int i) { return w1(cxi(i)) * w1(cyi(i)) * w1(czi(i)); }
+
+// Offsets of the 27 pulled populations of node (x, y, z): source x - c_i.
+// xo[k] = wrapped x - 1 + k, yo[k] = (wrapped y - 1 + k) * nx, zo[k] = (wrapped z - 1 + k) * nx*ny.
+struct Cell {
+    unsigned xo[3], yo[3];
+};
+
+__device__ __forceinline__ Cell cell_of(int x, int y, int nx, int ny)
+{
+    Cell c;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c.xo[k] = (unsigned)wrapi(x - 1 + k, nx);
+        c.yo[k] = (unsigned)wrapi(y - 1 + k, ny) * (unsigned)nx;
+    }
+    return c;
+}
+
+__device__ __forceinline__ void plane_offsets(int z, int nx, int ny, int nz, unsigned zo[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) zo[k] = (unsigned)wrapi(z - 1 + k, nz) * (unsigned)nx * (unsigned)ny;
+}
+
+// h_i = h~_i(x - c_i): index of the source of population i.
+__device__ __forceinline__ unsigned src_of(int i, const Cell &c, const unsigned zo[3], unsigned N)
+{
+    return (unsigned)i * N + zo[1 - czi(i)] + c.yo[1 - cyi(i)] + c.xo[1 - cxi(i)];
+}
+
+// Psi(c; xi, zeta): 1 - zeta (c = 0), (zeta +- xi)/2 (c = +-1), Eq. (phi).
+__device__ __forceinline__ void psi3(float xi, float zeta, float out[3])
+{
+    out[0] = 0.5f * (zeta - xi);
+    out[1] = 1.f - zeta;
+    out[2] = 0.5f * (zeta + xi);
+}
+
+// The same linear combination applied to (A0, A1, A2).
+__device__ __forceinline__ void psi3_poly(float A0, float A1, float A2, float out[3])
+{
+    out[0] = 0.5f * (A2 - A1);
+    out[1] = A0 - A2;
+    out[2] = 0.5f * (A2 + A1);
+}
+
+template <bool THERMAL>
+__global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
+{
+    extern __shared__ float sm[];
+    const int t = threadIdx.x;
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * A.HZ;
+    const int zend = min(z0 + A.HZ, nz);
+    const unsigned N = A.N;
+    const float a = A.a, b = A.b, kappa = A.kappa, lambda = A.lambda;
+
+    // Columns this thread handles in stages A, B, C (up to two each).
+    auto colA = [&](int k, int &cx, int &cy) { const int c = t + k * NT; cx = c % WA - 3; cy = c / WA - 3; return c < SA; };
+    auto colB = [&](int k, int &cx, int &cy) { const int c = t + k * NT; cx = c % WB - 2; cy = c / WB - 2; return c < SB; };
+    auto colC = [&](int k, int &cx, int &cy) { const int c = t + k * NT; cx = c % WC - 1; cy = c / WC - 1; return c < SC; };
+    auto sa = [](int cx, int cy) { return (cy + 3) * WA + (cx + 3); };
+    auto sb = [](int cx, int cy) { return (cy + 2) * WB + (cx + 2); };
+    auto sc = [](int cx, int cy) { return (cy + 1) * WC + (cx + 1); };
+    float *RHO = sm + O_RHO, *J = sm + O_J, *PI = sm + O_PI, *CF = sm + O_CF, *CEN = sm + O_CEN;
+
+    const int dcx = t % TX, dcy = t / TX;                 // this thread's output column
+    const bool inD = x0 + dcx < nx && y0 + dcy < ny;
+    const Cell cD = cell_of(x0 + dcx, y0 + dcy, nx, ny);
+
+    const int qbeg = z0 - 3, qend = zend + 2;
+    for (int q = qbeg; q <= qend; ++q) {
+        const int s0 = ((q % 3) + 3) % 3;                 // ring slot of plane q (and of q-3)
+        const int sm1 = s0 == 0 ? 2 : s0 - 1;             // plane q-1 (and q-4)
+        const int sm2 = s0 == 2 ? 0 : s0 + 1;             // plane q-2
+        // ---------------- A: rho, j of plane q ----------------
+        if (q <= zend + 2) {
+            unsigned zo[3];
+            plane_offsets(q, nx, ny, nz, zo);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                int cx, cy;
+                if (!colA(k, cx, cy)) continue;
+                const Cell c = cell_of(x0 + cx, y0 + cy, nx, ny);
+                float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+                for (int i = 0; i < 27; ++i) {
+                    const float h = __ldg(A.f + src_of(i, c, zo, N));
+                    rho += h;
+                    if (cxi(i) == 1) jx += h; else if (cxi(i) == -1) jx -= h;
+                    if (cyi(i) == 1) jy += h; else if (cyi(i) == -1) jy -= h;
+                    if (czi(i) == 1) jz += h; else if (czi(i) == -1) jz -= h;
+                }
+                RHO[s0 * SA + sa(cx, cy)] = rho;
+                if (cx >= -1 && cx <= TX && cy >= -1 && cy <= TY) {
+                    float *jr = J + s0 * 3 * SC + sc(cx, cy);
+                    jr[0] = jx;
+                    jr[SC] = jy;
+                    jr[2 * SC] = jz;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---------------- B: Korteweg stress of plane q-1 ----------------
+        if (q - 1 >= z0 - 2 && q - 1 <= zend + 1) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                int cx, cy;
+                if (!colB(k, cx, cy)) continue;
+                const float *r[3] = {RHO + sm2 * SA, RHO + sm1 * SA, RHO + s0 * SA};   // planes q-2, q-1, q
+                const int c0 = sa(cx, cy);
+                const float rc = r[1][c0];
+                float gx = 0.f, gy = 0.f, gz = 0.f, lap = 0.f;
+#pragma unroll
+                for (int i = 0; i < 27; ++i) {
+                    if (i == 13) continue;
+                    const float v = r[1 + czi(i)][c0 + cyi(i) * WA + cxi(i)];
+                    const float w = wi(i);
+                    if (cxi(i)) gx += (cxi(i) * w) * v;
+                    if (cyi(i)) gy += (cyi(i) * w) * v;
+                    if (czi(i)) gz += (czi(i) * w) * v;
+                    lap += w * (v - rc);
+                }
+                gx *= 3.f; gy *= 3.f; gz *= 3.f; lap *= 6.f;
+                const float s = -a * rc * rc - kappa * rc * lap - 0.5f * kappa * (gx * gx + gy * gy + gz * gz);
+                float *pr = PI + sm1 * 6 * SB + sb(cx, cy);
+                pr[0] = s + kappa * gx * gx;
+                pr[SB] = kappa * gx * gy;
+                pr[2 * SB] = kappa * gx * gz;
+                pr[3 * SB] = s + kappa * gy * gy;
+                pr[4 * SB] = kappa * gy * gz;
+                pr[5 * SB] = s + kappa * gz * gz;
+            }
+        }
+        __syncthreads();
+
+        // ---------------- C: F, u, T, EOS of plane q-2 ----------------
+        if (q - 2 >= z0 - 1 && q - 2 <= zend) {
+            unsigned zo[3];
+            if (THERMAL) plane_offsets(q - 2, nx, ny, nz, zo);
+            const int zc = wrapi(q - 2, nz);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                int cx, cy;
+                if (!colC(k, cx, cy)) continue;
+                // Pi of planes q-3 (slot s0), q-2 (sm2), q-1 (sm1).
+                const float *P[3] = {PI + s0 * 6 * SB, PI + sm2 * 6 * SB, PI + sm1 * 6 * SB};
+                const int b0 = sb(cx, cy);
+                // d_b Pi_ab with the isotropic gradient 3 sum_i w_i c_ib Pi_ab(x + c_i).
+                float dPi[6][3];                          // [component][direction]
+#pragma unroll
+                for (int m = 0; m < 6; ++m) dPi[m][0] = dPi[m][1] = dPi[m][2] = 0.f;
+#pragma unroll
+                for (int i = 0; i < 27; ++i) {
+                    if (i == 13) continue;
+                    const float w = wi(i);
+                    const float *pp = P[1 + czi(i)] + b0 + cyi(i) * WB + cxi(i);
+                    // Components needed: x-derivative of xx, xy, xz; y of xy, yy, yz; z of xz, yz, zz.
+                    if (cxi(i)) {
+                        const float cw = cxi(i) * w;
+                        dPi[0][0] += cw * pp[0];
+                        dPi[1][0] += cw * pp[SB];
+                        dPi[2][0] += cw * pp[2 * SB];
+                    }
+                    if (cyi(i)) {
+                        const float cw = cyi(i) * w;
+                        dPi[1][1] += cw * pp[SB];
+                        dPi[3][1] += cw * pp[3 * SB];
+                        dPi[4][1] += cw * pp[4 * SB];
+                    }
+                    if (czi(i)) {
+                        const float cw = czi(i) * w;
+                        dPi[2][2] += cw * pp[2 * SB];
+                        dPi[4][2] += cw * pp[4 * SB];
+                        dPi[5][2] += cw * pp[5 * SB];
+                    }
+                }
+                const float Fx = -3.f * (dPi[0][0] + dPi[1][1] + dPi[2][2]);
+                const float Fy = -3.f * (dPi[1][0] + dPi[3][1] + dPi[4][2]);
+                const float Fz = -3.f * (dPi[2][0] + dPi[4][1] + dPi[5][2]);
+                const float rho = RHO[sm2 * SA + sa(cx, cy)];
+                const float *jr = J + sm2 * 3 * SC + sc(cx, cy);
+                const float ir = __frcp_rn(rho);
+                const float ux = (jr[0] + 0.5f * Fx) * ir, uy = (jr[SC] + 0.5f * Fy) * ir, uz = (jr[2 * SC] + 0.5f * Fz) * ir;
+                float RT;
+                if (THERMAL) {
+                    const Cell c = cell_of(x0 + cx, y0 + cy, nx, ny);
+                    float Gam = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 27; ++i) Gam += __ldg(A.g + src_of(i, c, zo, N));
+                    const float E = (Gam + 0.5f * (ux * Fx + uy * Fy + uz * Fz)) * ir;
+                    RT = (2.f / 3.f) * (E - 0.5f * (ux * ux + uy * uy + uz * uz));
+                } else {
+                    const unsigned n = (unsigned)zc * (unsigned)nx * (unsigned)ny +
+                                       (unsigned)wrapi(y0 + cy, ny) * (unsigned)nx + (unsigned)wrapi(x0 + cx, nx);
+                    RT = __ldg(A.RT_iso + n);
+                }
+                // EOS in the Enskog gauge: P0 = P_E = rho RT Z, gamma0 = 1 + rho Z'/Z [+ 2/3 Z].
+                float Z, dlnZ;
+                if (A.eos == 0) {
+                    Z = __frcp_rn(1.f - b * rho);
+                    dlnZ = b * rho * Z;
+                } else {
+                    const float eta = 0.25f * b * rho;
+                    const float num = 1.f + eta + eta * eta - eta * eta * eta;
+                    const float iom = __frcp_rn(1.f - eta);
+                    Z = num * iom * iom * iom;
+                    dlnZ = eta * (4.f + 4.f * eta - 2.f * eta * eta) * iom * __frcp_rn(num);
+                }
+                const float g0 = THERMAL ? 1.f + dlnZ + (2.f / 3.f) * Z : 1.f + dlnZ;
+                const float th = RT * Z;
+                const float th3m1 = 3.f * th - 1.f;
+                float *cf = CF + sm2 * 7 * SC + sc(cx, cy);
+                cf[0] = ux;
+                cf[SC] = uy;
+                cf[2 * SC] = uz;
+                cf[3 * SC] = rho * ux * (ux * ux + th3m1);
+                cf[4 * SC] = rho * uy * (uy * uy + th3m1);
+                cf[5 * SC] = rho * uz * (uz * uz + th3m1);
+                cf[6 * SC] = th - RT;
+                if (cx >= 0 && cx < TX && cy >= 0 && cy < TY) {
+                    float *ce = CEN + (q & 1) * 7 * NT + cy * TX + cx;
+                    ce[0] = rho; ce[NT] = Fx; ce[2 * NT] = Fy; ce[3 * NT] = Fz;
+                    ce[4 * NT] = RT; ce[5 * NT] = th; ce[6 * NT] = g0;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---------------- D: collide plane q-3 ----------------
+        const int p = q - 3;
+        if (p >= z0 && p < zend && inD) {
+            const float *ce = CEN + ((q - 1) & 1) * 7 * NT + t;    // stage C of plane p ran at iteration q-1
+            const float rho = ce[0], Fx = ce[NT], Fy = ce[2 * NT], Fz = ce[3 * NT];
+            const float RT = ce[4 * NT], th = ce[5 * NT], g0 = ce[6 * NT];
+            // C fields of planes p-1 (slot sm1), p (s0), p+1 (sm2).
+            const float *Fm = CF + sm1 * 7 * SC, *F0 = CF + s0 * 7 * SC, *Fp = CF + sm2 * 7 * SC;
+            const int c0 = sc(dcx, dcy);
+            const int xp = c0 + 1, xm = c0 - 1, yp = c0 + WC, ym = c0 - WC;
+            const float ux = F0[c0], uy = F0[SC + c0], uz = F0[2 * SC + c0];
+            const float P0 = rho * th;
+            const float divu = 0.5f * ((F0[xp] - F0[xm]) + (F0[SC + yp] - F0[SC + ym]) + (Fp[2 * SC + c0] - Fm[2 * SC + c0]));
+            const float Phi1 = P0 * (5.f / 3.f - g0) * divu;
+            // Phi_aa = Phi' - d_a[rho u_a (u_a^2 + 3 theta0 - 1)] (sign cancelling the c^3 = c bias).
+            const float Phx = Phi1 - 0.5f * (F0[3 * SC + xp] - F0[3 * SC + xm]);
+            const float Phy = Phi1 - 0.5f * (F0[4 * SC + yp] - F0[4 * SC + ym]);
+            const float Phz = Phi1 - 0.5f * (Fp[5 * SC + c0] - Fm[5 * SC + c0]);
+            const float lP0h = 0.5f * lambda * P0, lPhi = lambda * Phi1;
+            const float qx = lP0h * (F0[6 * SC + xp] - F0[6 * SC + xm]) + ux * lPhi;
+            const float qy = lP0h * (F0[6 * SC + yp] - F0[6 * SC + ym]) + uy * lPhi;
+            const float qz = lP0h * (Fp[6 * SC + c0] - Fm[6 * SC + c0]) + uz * lPhi;
+
+            const float lir = lambda * __frcp_rn(rho);
+            const float usx = ux + Fx * lir, usy = uy + Fy * lir, usz = uz + Fz * lir;
+            // Separable equilibria: h_i = X[c_ix] * YZ[c_iy][c_iz] (+ X'[c_ix] * YZ'[..]),
+            // the per-axis Psi factors combined once per node (Eqs. feq, f_star, geq, gstar).
+            float ex[3], ey[3], ez[3], sx[3], sy[3], sz[3];
+            psi3(ux, th + ux * ux, ex);
+            psi3(uy, th + uy * uy, ey);
+            psi3(uz, th + uz * uz, ez);
+            psi3(usx, th + usx * usx + Phx * lir, sx);
+            psi3(usy, th + usy * usy + Phy * lir, sy);
+            psi3(usz, th + usz * usz + Phz * lir, sz);
+            float rex[3], rsx[3], Eyz[9], Syz[9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                rex[k] = rho * ex[k];
+                rsx[k] = rho * sx[k];
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    Eyz[3 * j + k] = ey[j] * ez[k];
+                    Syz[3 * j + k] = sy[j] * sz[k];
+                }
+
+            unsigned zo[3];
+            plane_offsets(p, nx, ny, nz, zo);
+            const unsigned out = (unsigned)wrapi(p, nz) * (unsigned)nx * (unsigned)ny +
+                                 (unsigned)(y0 + dcy) * (unsigned)nx + (unsigned)(x0 + dcx);
+            const float kh = 1.f - A.c_eq, keq = A.c_eq - A.c_star, kst = A.c_star;
+#pragma unroll
+            for (int i = 0; i < 27; ++i) {
+                const int ix = cxi(i) + 1, iyz = 3 * (cyi(i) + 1) + czi(i) + 1;
+                const float h = __ldg(A.f + src_of(i, cD, zo, N));
+                A.fo[(unsigned)i * N + out] = kh * h + keq * (rex[ix] * Eyz[iyz]) + kst * (rsx[ix] * Syz[iyz]);
+            }
+            if (THERMAL) {
+                // g^eq_i = rho [e PP_x PP_y PP_z + PS_x PP_y PP_z + PP_x PS_y PP_z + PP_x PP_y PS_z]
+                //        = rho (e PP_x + PS_x) [PP_y PP_z] + rho PP_x [PS_y PP_z + PP_y PS_z],
+                // e = 3/2 RT, PP = Psi(u, theta0 + u^2), PS = Psi applied to (u^2/2,
+                // theta0 u + u^3/2, theta0^2 + 5/2 theta0 u^2 + u^4/2); g* the same at
+                // (u*, RT*) without Phi, plus g' = 1/2 c_i . q' on the |c| = 1 populations.
+                const float e = 1.5f * RT;
+                const float es = e - 0.5f * (Fx * Fx + Fy * Fy + Fz * Fz) * (lir * lir);
+                auto psiS = [&](float v, float o3[3]) {
+                    const float vv = v * v;
+                    psi3_poly(0.5f * vv, v * (th + 0.5f * vv), th * th + vv * (2.5f * th + 0.5f * vv), o3);
+                };
+                float S[3], T[3], px[3], py[3], pz[3];
+                float Ag[3], As[3], rpx[3], Cyz[9], Pyz[9], Dyz[9];
+                psiS(ux, S);
+                psi3(usx, th + usx * usx, px);
+                psiS(usx, T);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    Ag[k] = rho * (e * ex[k] + S[k]);
+                    rpx[k] = rho * px[k];
+                    As[k] = rho * (es * px[k] + T[k]);
+                }
+                float Sy[3], Sz[3], Ty[3], Tz[3];
+                psiS(uy, Sy);
+                psiS(uz, Sz);
+                psiS(usy, Ty);
+                psiS(usz, Tz);
+                psi3(usy, th + usy * usy, py);
+                psi3(usz, th + usz * usz, pz);
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        Cyz[3 * j + k] = Sy[j] * ez[k] + ey[j] * Sz[k];
+                        Pyz[3 * j + k] = py[j] * pz[k];
+                        Dyz[3 * j + k] = Ty[j] * pz[k] + py[j] * Tz[k];
+                    }
+                const float hq[3] = {0.5f * qx, 0.5f * qy, 0.5f * qz};
+#pragma unroll
+                for (int i = 0; i < 27; ++i) {
+                    const int ix = cxi(i) + 1, iyz = 3 * (cyi(i) + 1) + czi(i) + 1;
+                    const float h = __ldg(A.g + src_of(i, cD, zo, N));
+                    const float geq = Ag[ix] * Eyz[iyz] + rex[ix] * Cyz[iyz];
+                    float gst = As[ix] * Pyz[iyz] + rpx[ix] * Dyz[iyz];
+                    if (abs(cxi(i)) + abs(cyi(i)) + abs(czi(i)) == 1)
+                        gst += (cxi(i) ? cxi(i) * hq[0] : 0.f) + (cyi(i) ? cyi(i) * hq[1] : 0.f) +
+                               (czi(i) ? czi(i) * hq[2] : 0.f);
+                    A.go[(unsigned)i * N + out] = kh * h + keq * geq + kst * gst;
+                }
+            }
+        }
+    }
+}
+
+template <bool THERMAL>
+cudaError_t launch(const Args &A, cudaStream_t st)
+{
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (attr_dev != dev) {
+        e = cudaFuncSetAttribute(k_fused3d<THERMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY, (A.nz + A.HZ - 1) / A.HZ);
+    k_fused3d<THERMAL><<<grid, NT, SMEM_BYTES, st>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused3d_supported(int prec, int Q, const KParams &p)
+{
+    return prec == 1 && Q == 27 && p.force_form == 0 && (long long)27 * p.N < (1LL << 31);
+}
+
+cudaError_t fused3d_step(const KParams &p, const void *f, const void *g, void *fo, void *go, const void *RT_iso,
+                         cudaStream_t st)
+{
+    Args A;
+    A.f = static_cast<const float *>(f);
+    A.g = static_cast<const float *>(g);
+    A.fo = static_cast<float *>(fo);
+    A.go = static_cast<float *>(go);
+    A.RT_iso = static_cast<const float *>(RT_iso);
+    A.nx = p.nx;
+    A.ny = p.ny;
+    A.nz = p.nz;
+    A.N = (unsigned)p.N;
+    A.eos = p.eos;
+    A.a = float(p.a);
+    A.b = float(p.b);
+    A.kappa = float(p.kappa);
+    A.lambda = float(p.lambda);
+    A.c_eq = float(p.c_eq);
+    A.c_star = float(p.c_star);
+    A.HZ = p.tile_h > 0 ? p.tile_h : (p.nz < 64 ? p.nz : 64);
+    return p.thermal ? launch<true>(A, st) : launch<false>(A, st);
+}
+
+}  // namespace evlbm
