@@ -345,8 +345,10 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
 #pragma unroll
             for (int i = 0; i < 27; ++i) {
                 const int ix = cxi(i) + 1, iyz = 3 * (cyi(i) + 1) + czi(i) + 1;
+                // The output is not read again this step: a streaming store keeps L2 for
+                // the populations the stages still share.
                 const float h = __ldg(A.f + src_of(i, cD, zo, N));
-                A.fo[(unsigned)i * N + out] = kh * h + keq * (rex[ix] * Eyz[iyz]) + kst * (rsx[ix] * Syz[iyz]);
+                __stcs(A.fo + (unsigned)i * N + out, kh * h + keq * (rex[ix] * Eyz[iyz]) + kst * (rsx[ix] * Syz[iyz]));
             }
             if (THERMAL) {
                 // g^eq_i = rho [e PP_x PP_y PP_z + PS_x PP_y PP_z + PP_x PS_y PP_z + PP_x PP_y PS_z]
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                     if (abs(cxi(i)) + abs(cyi(i)) + abs(czi(i)) == 1)
                         gst += (cxi(i) ? cxi(i) * hq[0] : 0.f) + (cyi(i) ? cyi(i) * hq[1] : 0.f) +
                                (czi(i) ? czi(i) * hq[2] : 0.f);
-                    A.go[(unsigned)i * N + out] = kh * h + keq * geq + kst * gst;
+                    __stcs(A.go + (unsigned)i * N + out, kh * h + keq * geq + kst * gst);
                 }
             }
         }
