@@ -87,7 +87,12 @@ __device__ __forceinline__ int wrap_any(int v, int n)
 __device__ __forceinline__ int prev_row(int r, int ny) { return r == 0 ? ny - 1 : r - 1; }
 __device__ __forceinline__ int next_row(int r, int ny) { return r == ny - 1 ? 0 : r + 1; }
 
-template <bool CG> __device__ __forceinline__ float ldpop(const float *p) { return CG ? __ldcg(p) : __ldg(p); }
+// CG: the populations were written earlier in the same launch (persistent ensemble kernel),
+// so the read-only path (ld.global.nc) is not allowed.  A plain L1-cached load (ld.global.ca)
+// is: the CTA reads them only after thread 0's gpu-scope acquire of the domain's completion
+// counter (which pairs with the producers' fence + atomic release) and a CTA barrier, and an
+// acquire at gpu scope makes every later load of the CTA observe the released writes.
+template <bool CG> __device__ __forceinline__ float ldpop(const float *p) { return CG ? __ldca(p) : __ldg(p); }
 
 // Pulled populations of rows (r, r+1) of one column: h_i(y) = h~_i(x - c_ix, y - c_iy).
 // ro[k] = offset of wrapped row r - 1 + k (k = 0..3), cols[k] = wrapped column x - 1 + k.
