@@ -46,7 +46,15 @@ __device__ __forceinline__ v2 operator*(v2 a, v2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ v2 operator-(v2 a, v2 b) { return __ffma2_rn(b, V(-1.f), a); }
 __device__ __forceinline__ v2 operator-(v2 a) { return __fmul2_rn(a, V(-1.f)); }
 __device__ __forceinline__ v2 fma2(v2 a, v2 b, v2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ v2 rcp2(v2 a) { return V(__frcp_rn(a.x), __frcp_rn(a.y)); }
+// Reciprocal with the hardware approximation (rcp.approx.ftz: at most 1 ulp, relative
+// error below 2^-22); the operands (rho, 1 - b rho, EOS polynomials) are normal numbers.
+__device__ __forceinline__ float rcpa(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ v2 rcp2(v2 a) { return V(rcpa(a.x), rcpa(a.y)); }
 // (lo.y, hi.x): the row pair shifted by one row.
 __device__ __forceinline__ v2 shift_up(v2 lo, v2 hi) { return V(lo.y, hi.x); }
 
@@ -350,7 +358,14 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
             const v2 sx[3] = {hr * (zsx - usx), rho - rho * zsx, hr * (zsx + usx)};
             const v2 sy[3] = {V(0.5f) * (zsy - usy), V(1.f) - zsy, V(0.5f) * (zsy + usy)};
 
+            // Collision f' = kh f + keq f^eq + kst f*: the weights are folded into the x factors.
             const v2 kh = V(1.f - A.c_eq), keq = V(A.c_eq - A.c_star), kst = V(A.c_star);
+            v2 exk[3], sxk[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                exk[k] = keq * ex[k];
+                sxk[k] = kst * sx[k];
+            }
             const unsigned out0 = layer + (unsigned)rD * nx + cols[1];
             const unsigned out1 = layer + (unsigned)next_row(rD, ny) * nx + cols[1];
             const bool second = 2 * p + 1 < y0 + Heff;
@@ -358,7 +373,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const int ix = i % 3, iy = i / 3;
-                const v2 o = fma2(kh, fr[i * kW], fma2(keq, ex[ix] * ey[iy], kst * (sx[ix] * sy[iy])));
+                const v2 o = fma2(kh, fr[i * kW], fma2(exk[ix], ey[iy], sxk[ix] * sy[iy]));
                 A.fo[i * N + out0] = o.x;
                 if (second) A.fo[i * N + out1] = o.y;
             }
@@ -382,24 +397,26 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
                 // PsiP at the shifted velocity (no Phi: that correction belongs to f* only).
                 const v2 px[3] = {hr * (zpx - usx), rho - rho * zpx, hr * (zpx + usx)};
                 const v2 py[3] = {V(0.5f) * (zpy - usy), V(1.f) - zpy, V(0.5f) * (zpy + usy)};
-                v2 Ax[3], As[3];
+                // x factors pre-multiplied by the collision weights keq (g^eq) and kst (g*).
+                v2 Ax[3], As[3], pxk[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    Ax[k] = fma2(e, ex[k], rho * Sx[k]);      // rho (e PsiP_x + PsiS_x)
-                    As[k] = fma2(es, px[k], rho * SSx[k]);
+                    Ax[k] = keq * fma2(e, ex[k], rho * Sx[k]);      // keq rho (e PsiP_x + PsiS_x)
+                    As[k] = kst * fma2(es, px[k], rho * SSx[k]);
+                    pxk[k] = kst * px[k];
                 }
-                const v2 hqx = V(0.5f) * qx, hqy = V(0.5f) * qy;
+                const v2 hqx = V(0.5f * A.c_star) * qx, hqy = V(0.5f * A.c_star) * qy;
                 const v2 *gr = g9 + (p & 1) * 9 * kW + t;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const int ix = i % 3, iy = i / 3;
-                    const v2 geq = fma2(Ax[ix], ey[iy], ex[ix] * Sy[iy]);
-                    v2 gst = fma2(As[ix], py[iy], px[ix] * SSy[iy]);
-                    if (i == 1) gst = gst - hqy;   // c = (0,-1)
-                    if (i == 3) gst = gst - hqx;   // c = (-1,0)
-                    if (i == 5) gst = gst + hqx;   // c = (1,0)
-                    if (i == 7) gst = gst + hqy;   // c = (0,1)
-                    const v2 o = fma2(kh, gr[i * kW], fma2(keq, geq, kst * gst));
+                    v2 c = fma2(As[ix], py[iy], pxk[ix] * SSy[iy]);          // kst g*
+                    if (i == 1) c = c - hqy;   // c = (0,-1)
+                    if (i == 3) c = c - hqx;   // c = (-1,0)
+                    if (i == 5) c = c + hqx;   // c = (1,0)
+                    if (i == 7) c = c + hqy;   // c = (0,1)
+                    c = fma2(exk[ix], Sy[iy], fma2(Ax[ix], ey[iy], c));      // + keq g^eq
+                    const v2 o = fma2(kh, gr[i * kW], c);
                     A.go[i * N + out0] = o.x;
                     if (second) A.go[i * N + out1] = o.y;
                 }

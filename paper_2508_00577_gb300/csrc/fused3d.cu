@@ -47,6 +47,15 @@ struct Args {
     float a, b, kappa, lambda, c_eq, c_star;
 };
 
+// Reciprocal with the hardware approximation (rcp.approx.ftz: at most 1 ulp); the
+// operands (rho, 1 - b rho, EOS polynomials) are normal numbers.
+__device__ __forceinline__ float rcpa(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
 __device__ __forceinline__ int wrapi(int v, int n)
 {
     v %= n;
@@ -242,7 +251,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                 const float Fz = -3.f * (dPi[2][0] + dPi[4][1] + dPi[5][2]);
                 const float rho = RHO[sm2 * SA + sa(cx, cy)];
                 const float *jr = J + sm2 * 3 * SC + sc(cx, cy);
-                const float ir = __frcp_rn(rho);
+                const float ir = rcpa(rho);
                 const float ux = (jr[0] + 0.5f * Fx) * ir, uy = (jr[SC] + 0.5f * Fy) * ir, uz = (jr[2 * SC] + 0.5f * Fz) * ir;
                 float RT;
                 if (THERMAL) {
@@ -260,14 +269,14 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                 // EOS in the Enskog gauge: P0 = P_E = rho RT Z, gamma0 = 1 + rho Z'/Z [+ 2/3 Z].
                 float Z, dlnZ;
                 if (A.eos == 0) {
-                    Z = __frcp_rn(1.f - b * rho);
+                    Z = rcpa(1.f - b * rho);
                     dlnZ = b * rho * Z;
                 } else {
                     const float eta = 0.25f * b * rho;
                     const float num = 1.f + eta + eta * eta - eta * eta * eta;
-                    const float iom = __frcp_rn(1.f - eta);
+                    const float iom = rcpa(1.f - eta);
                     Z = num * iom * iom * iom;
-                    dlnZ = eta * (4.f + 4.f * eta - 2.f * eta * eta) * iom * __frcp_rn(num);
+                    dlnZ = eta * (4.f + 4.f * eta - 2.f * eta * eta) * iom * rcpa(num);
                 }
                 const float g0 = THERMAL ? 1.f + dlnZ + (2.f / 3.f) * Z : 1.f + dlnZ;
                 const float th = RT * Z;
@@ -312,7 +321,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
             const float qy = lP0h * (F0[6 * SC + yp] - F0[6 * SC + ym]) + uy * lPhi;
             const float qz = lP0h * (Fp[6 * SC + c0] - Fm[6 * SC + c0]) + uz * lPhi;
 
-            const float lir = lambda * __frcp_rn(rho);
+            const float lir = lambda * rcpa(rho);
             const float usx = ux + Fx * lir, usy = uy + Fy * lir, usz = uz + Fz * lir;
             // Separable equilibria: h_i = X[c_ix] * YZ[c_iy][c_iz] (+ X'[c_ix] * YZ'[..]),
             // the per-axis Psi factors combined once per node (Eqs. feq, f_star, geq, gstar).
