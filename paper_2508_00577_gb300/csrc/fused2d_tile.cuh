@@ -22,8 +22,11 @@
 //   C: F, u, T, EOS (q-2)      div Pi of pairs q-3..q-1, Gamma     (W + 2 columns)
 //   D: collide (q-3)           Phi, q' from the fields of q-4..q-2 (W columns)
 // Fields shared between columns live in 3-deep shared-memory rings of row
-// pairs; the pulled f (stage A -> D), the pulled g (C -> D) and the centre
-// values (C -> D) of a column live in thread-private shared-memory rings.  The 6
+// pairs; the pulled f (stage A -> D) and the pulled g (C -> D) of a column live in
+// thread-private shared-memory rings, its centre values (C -> D) in a one-pair slot
+// that the thread reads before it rewrites it.  Shared memory stays under 97 KiB per
+// CTA so that two CTAs leave the L1 60 KB: every global load in flight holds L1
+// space, and a 28 KB L1 caps the loads in flight well below HBM bandwidth.  The 6
 // halo columns of a strip belong to an extra warp that runs stages A-C only.
 // Loads of the next f and g rows are issued one iteration ahead.  Every
 // population is read from HBM once per step; re-reads of halo columns are
@@ -74,7 +77,7 @@ template <int W> constexpr int threads_of() { return W + 32; }
 template <int W> constexpr int slots_of() { return W + 6; }
 template <int W> constexpr size_t smem_of()
 {
-    return sizeof(v2) * (size_t)(kFields * kDepth * slots_of<W>() + (4 * 9 + 2 * 9 + 2 * kCentre) * W);
+    return sizeof(v2) * (size_t)(kFields * kDepth * slots_of<W>() + (4 * 9 + 2 * 9 + kCentre) * W);
 }
 
 struct FusedArgs {
@@ -132,7 +135,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
     auto fld = [&](int field, int slot3) -> v2 * { return smem + (field * kDepth + slot3) * S; };
     v2 *const f9 = smem + kFields * kDepth * S;          // [4][9][kW]   pulled f, stage A -> D
     v2 *const g9 = f9 + 4 * 9 * kW;                      // [2][9][kW]   pulled g, stage C -> D
-    v2 *const cen = g9 + 2 * 9 * kW;                     // [2][kCentre][kW]
+    v2 *const cen = g9 + 2 * 9 * kW;                     // [kCentre][kW]: one pair, read before rewritten
 
     const int nx = A.nx, ny = A.ny;
     const int t = threadIdx.x;
@@ -246,6 +249,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
         __syncthreads();
 
         // ---------------- C: force, velocity, temperature, EOS of pair q-2 ----------------
+        v2 cprev[kCentre];                                 // centre values of pair q-3 (stage D)
         if (inC && q - 2 >= q0 - 1) {
             // Pi of pairs q-3 (slot s0), q-2 (sm2, centre rows), q-1 (sm1).
             const int sw = slot - 1, se = slot + 1;
@@ -313,7 +317,11 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
             fld(QY, sm2)[slot] = rho * uy * fma2(uy, uy, th3m1);
             fld(WQ, sm2)[slot] = th - RT;
             if (inD) {
-                v2 *cr = cen + (q & 1) * kCentre * kW + t;
+                // The slot still holds pair q-3, which stage D collides later in this
+                // iteration: take it into registers before storing pair q-2.
+                v2 *cr = cen + t;
+#pragma unroll
+                for (int k = 0; k < kCentre; ++k) cprev[k] = cr[k * kW];
                 cr[0 * kW] = rho; cr[1 * kW] = Fx; cr[2 * kW] = Fy;
                 cr[3 * kW] = RT; cr[4 * kW] = th; cr[5 * kW] = g0;
             }
@@ -323,8 +331,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
         // ---------------- D: collide pair q-3 ----------------
         if (inD && q - 3 >= q0) {
             const int p = q - 3;                   // its stage C ran at iteration q-1
-            const v2 *cr = cen + ((q - 1) & 1) * kCentre * kW + t;
-            const v2 rho = cr[0], Fx = cr[kW], Fy = cr[2 * kW], RT = cr[3 * kW], th = cr[4 * kW], g0 = cr[5 * kW];
+            const v2 rho = cprev[0], Fx = cprev[1], Fy = cprev[2], RT = cprev[3], th = cprev[4], g0 = cprev[5];
             const int sw = slot - 1, se = slot + 1;
             // fields of pairs p-1 (slot sm1), p (s0), p+1 (sm2)
             const v2 *uxp = fld(UX, s0), *qxp = fld(QX, s0);
