@@ -34,7 +34,7 @@ A, B, KAPPA, TAU = 0.1, 4.0, 0.116, 0.3
 BYTES_PER_LU = 2 * 9 * 2 * 4          # D2Q9, f and g, read + write, FP32
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fused2d launch on this workload
 # (profiles/fused2d_d2q9_thermal_fp32.md); None whenever the kernel changes.
-MEASURED_TRAFFIC_BYTES = 1.3398e9
+MEASURED_TRAFFIC_BYTES = 1.3353e9
 WORKLOAD = "droplet Laplace sweep: 9 x 1024^2 D2Q9 thermal, FP32"
 
 
