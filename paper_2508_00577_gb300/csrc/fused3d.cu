@@ -17,7 +17,9 @@
 //   D: collide (q-3)               u, T fields of q-4..q-2, populations pulled
 //                                  again (L2 hits: stage A/C read them 3/1 planes ago)
 // Shared fields live in 3-deep plane rings sized to the region that reads them;
-// centre values pass from C to D through a 2-deep per-thread ring.
+// centre values pass from C to D through a one-plane per-thread slot (stage C takes
+// the tile column a thread collides in D first, and reads the slot before rewriting
+// it); at 80.7 KB per CTA two CTAs leave the L1 ~92 KB for loads in flight.
 #include "dispatch.h"
 
 namespace evlbm {
@@ -33,8 +35,8 @@ constexpr int O_RHO = 0;                          // [3][SA]
 constexpr int O_J = O_RHO + 3 * SA;               // [3 planes][3 comps][SC]
 constexpr int O_PI = O_J + 9 * SC;                // [3 planes][6 comps][SB]  xx xy xz yy yz zz
 constexpr int O_CF = O_PI + 18 * SB;              // [3 planes][7][SC]  ux uy uz qx qy qz wq
-constexpr int O_CEN = O_CF + 21 * SC;             // [2][7][NT]  rho Fx Fy Fz RT theta0 gamma0
-constexpr int SMEM_FLOATS = O_CEN + 14 * NT;
+constexpr int O_CEN = O_CF + 21 * SC;             // [7][NT]  rho Fx Fy Fz RT theta0 gamma0 (one plane)
+constexpr int SMEM_FLOATS = O_CEN + 7 * NT;
 constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
 
 struct Args {
@@ -128,7 +130,17 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
     // Columns this thread handles in stages A, B, C (up to two each).
     auto colA = [&](int k, int &cx, int &cy) { const int c = t + k * NT; cx = c % WA - 3; cy = c / WA - 3; return c < SA; };
     auto colB = [&](int k, int &cx, int &cy) { const int c = t + k * NT; cx = c % WB - 2; cy = c / WB - 2; return c < SB; };
-    auto colC = [&](int k, int &cx, int &cy) { const int c = t + k * NT; cx = c % WC - 1; cy = c / WC - 1; return c < SC; };
+    // Stage C: first the tile's own column of this thread (the one it collides in stage D,
+    // so the centre values stay thread-private), then the 68 ring columns on threads 0..67.
+    auto colC = [&](int k, int &cx, int &cy) {
+        if (k == 0) { cx = t % TX; cy = t / TX; return true; }
+        const int r = t;
+        if (r < WC) { cx = r - 1; cy = -1; }
+        else if (r < 2 * WC) { cx = r - WC - 1; cy = TY; }
+        else if (r < 2 * WC + TY) { cx = -1; cy = r - 2 * WC; }
+        else { cx = TX; cy = r - 2 * WC - TY; }
+        return r < 2 * WC + 2 * TY;
+    };
     auto sa = [](int cx, int cy) { return (cy + 3) * WA + (cx + 3); };
     auto sb = [](int cx, int cy) { return (cy + 2) * WB + (cx + 2); };
     auto sc = [](int cx, int cy) { return (cy + 1) * WC + (cx + 1); };
@@ -206,6 +218,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
         __syncthreads();
 
         // ---------------- C: F, u, T, EOS of plane q-2 ----------------
+        float cprev[7];                                   // centre values of plane q-3 (stage D)
         if (q - 2 >= z0 - 1 && q - 2 <= zend) {
             unsigned zo[3];
             if (THERMAL) plane_offsets(q - 2, nx, ny, nz, zo);
@@ -289,8 +302,12 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                 cf[4 * SC] = rho * uy * (uy * uy + th3m1);
                 cf[5 * SC] = rho * uz * (uz * uz + th3m1);
                 cf[6 * SC] = th - RT;
-                if (cx >= 0 && cx < TX && cy >= 0 && cy < TY) {
-                    float *ce = CEN + (q & 1) * 7 * NT + cy * TX + cx;
+                if (k == 0) {
+                    // The slot still holds plane q-3, collided by this thread in stage D of
+                    // this iteration: take it into registers before storing plane q-2.
+                    float *ce = CEN + t;
+#pragma unroll
+                    for (int m = 0; m < 7; ++m) cprev[m] = ce[m * NT];
                     ce[0] = rho; ce[NT] = Fx; ce[2 * NT] = Fy; ce[3 * NT] = Fz;
                     ce[4 * NT] = RT; ce[5 * NT] = th; ce[6 * NT] = g0;
                 }
@@ -301,9 +318,9 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
         // ---------------- D: collide plane q-3 ----------------
         const int p = q - 3;
         if (p >= z0 && p < zend && inD) {
-            const float *ce = CEN + ((q - 1) & 1) * 7 * NT + t;    // stage C of plane p ran at iteration q-1
-            const float rho = ce[0], Fx = ce[NT], Fy = ce[2 * NT], Fz = ce[3 * NT];
-            const float RT = ce[4 * NT], th = ce[5 * NT], g0 = ce[6 * NT];
+            // Centre values of plane p (stage C ran at iteration q-1), read in stage C.
+            const float rho = cprev[0], Fx = cprev[1], Fy = cprev[2], Fz = cprev[3];
+            const float RT = cprev[4], th = cprev[5], g0 = cprev[6];
             // C fields of planes p-1 (slot sm1), p (s0), p+1 (sm2).
             const float *Fm = CF + sm1 * 7 * SC, *F0 = CF + s0 * 7 * SC, *Fp = CF + sm2 * 7 * SC;
             const int c0 = sc(dcx, dcy);

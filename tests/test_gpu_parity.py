@@ -147,6 +147,29 @@ def test_fp32_d2q9(nx, ny, nz):
     assert rel_rho_err(o, g) <= 1e-5
 
 
+@pytest.mark.parametrize("thermal", [1, 0])
+@pytest.mark.parametrize("nx,ny,nz,hz", [(20, 18, 11, 0), (33, 16, 7, 4), (16, 16, 16, 5), (5, 3, 4, 0),
+                                         (40, 35, 9, 3)])
+def test_fp32_d3q27(nx, ny, nz, hz, thermal):
+    """FP32 D3Q27 (fused single-pass kernel): max |d rho|/rho <= 1e-5 over 10 steps of a
+    spinodal state with 5 % density noise.  Edges that are not multiples of the 16 x 16
+    tile, odd plane counts, z-chunks that do not divide nz (hz; 0 = default chunk) and a
+    lattice smaller than one tile."""
+    _, Tc = E.critical_point(E.CS, A, B)
+    RT = 0.85 * Tc
+    s1, s2 = E.spinodal(E.CS, A, B, RT)
+    kappa = E.kappa_for_width(E.CS, A, B, RT, 4.0)
+    fields = inputs.spinodal_noise(nx, ny, nz, 0.5 * (s1 + s2), RT, amplitude=0.05, D=3)
+    o, g = pair(27, nx, ny, nz, fields, kappa, ev.LBM_FP32, thermal=thermal)
+    with g:
+        if hz:
+            ev.lbm_set_tile(g.ctx, 16, hz)
+        assert ev.lbm_launches_per_step(g.ctx) == 1       # the fused kernel, not the stage kernels
+        o.step(10)
+        g.step(10)
+        assert rel_rho_err(o, g) <= 1e-5
+
+
 @pytest.mark.parametrize("nx,ny", [(64, 48), (300, 40)])
 def test_fp32_d2q9_isothermal(nx, ny):
     fields, kappa = droplet_fields(nx, ny, 1, tr=0.9)
