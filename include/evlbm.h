@@ -45,6 +45,7 @@ extern "C" {
 #define LBM_ENOMEM (-3)      /* device or host allocation failed */
 #define LBM_ENONFINITE (-4)  /* a NaN or Inf was found in the state */
 #define LBM_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
+#define LBM_EIO (-6)         /* a checkpoint file could not be written or read */
 
 #define LBM_D2Q9 0
 #define LBM_D3Q27 1
@@ -130,6 +131,35 @@ int lbm_conserved(lbm_ctx *ctx, double out[5]);
 
 /* Number of time steps taken since lbm_init. */
 long long lbm_step_count(const lbm_ctx *ctx);
+
+/* Checkpoint and resume.  The method has no state beyond the post-collision
+ * populations of Eq. (pre_LBM) (plus, per storage type, the per-node reference
+ * states of 16-bit deviation storage and the frozen R T field when thermal = 0),
+ * so a checkpoint holds exactly those device buffers, byte for byte in the
+ * context's own storage format, with the step count and every lbm_params field:
+ * a resumed run is bit-identical to one that never stopped.
+ *
+ * lbm_save writes `path` (first to "<path>.tmp", then renamed over `path`, so an
+ * interrupted save never leaves a partial file under the final name).  It waits
+ * for the work queued on the context's stream.  Layout (little-endian): the
+ * 8 bytes "EVLBMCKP", u32 version (1), u32 0, i32 lattice nx ny nz eos thermal
+ * precision force_form, f64 a b R kappa tau lambda, i64 step count, u64 byte
+ * counts of the four sections (f, g, reference states, frozen R T; 0 when
+ * absent), then the sections in that order.  The host is staged through a
+ * buffer of at most 64 MiB.
+ *
+ * lbm_load reads such a file into an existing context created with the same
+ * lbm_params (every field must match; the initial fields given to lbm_init do
+ * not matter) and restores its step count.  The launch shape (lbm_set_tile) is
+ * not part of the state and is kept.
+ *
+ * Errors: LBM_EINVAL (NULL arguments, not a checkpoint of this library, another
+ * version, or parameters or sizes that differ from the context's; the message
+ * names the field), LBM_EIO (the file cannot be opened, written or read, or is
+ * truncated), LBM_ENOMEM (host staging buffer), LBM_ECUDA.  On an error lbm_load
+ * may have overwritten part of the state. */
+int lbm_save(lbm_ctx *ctx, const char *path);
+int lbm_load(lbm_ctx *ctx, const char *path);
 
 /* Number of kernel launches one lbm_step time step enqueues for this context
  * (1 for the fused single-pass kernel, 4 for the stage-by-stage kernels);

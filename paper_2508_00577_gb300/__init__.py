@@ -19,18 +19,18 @@ __all__ = [
     "lbm_populations", "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_set_tile",
     "lbm_get_tile", "lbm_autotune", "lbm_sync", "lbm_free",
     "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "lbm_step_noalloc", "lbm_reset_device",
-    "LBMError", "Lattice",
+    "lbm_save", "lbm_load", "LBMError", "Lattice",
     "LBM_D2Q9", "LBM_D3Q27", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
     "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS", "Batch",
 ]
 
-LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENOMEM, LBM_ENONFINITE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5
+LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENOMEM, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EIO = 0, -1, -2, -3, -4, -5, -6
 LBM_D2Q9, LBM_D3Q27 = 0, 1
 LBM_EOS_VDW, LBM_EOS_CS = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
 
 _ERRNAMES = {LBM_EINVAL: "LBM_EINVAL", LBM_ECUDA: "LBM_ECUDA", LBM_ENOMEM: "LBM_ENOMEM",
-             LBM_ENONFINITE: "LBM_ENONFINITE", LBM_ETIMEOUT: "LBM_ETIMEOUT"}
+             LBM_ENONFINITE: "LBM_ENONFINITE", LBM_ETIMEOUT: "LBM_ETIMEOUT", LBM_EIO: "LBM_EIO"}
 
 # Every symbol include/evlbm.h declares.
 EXPORTED_SYMBOLS = (
@@ -39,7 +39,7 @@ EXPORTED_SYMBOLS = (
     "lbm_autotune", "lbm_sync", "lbm_free", "lbm_last_error", "lbm_coexistence", "lbm_critical_point",
     "lbm_step_noalloc", "lbm_batch_init", "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_tile",
     "lbm_batch_get_tile", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_batch_nodes",
-    "lbm_batch_free", "lbm_batch_last_error", "lbm_reset_device",
+    "lbm_batch_free", "lbm_batch_last_error", "lbm_reset_device", "lbm_save", "lbm_load",
 )
 
 
@@ -100,6 +100,8 @@ def lib():
             L.lbm_populations.argtypes = [vp, dp, dp]
             L.lbm_conserved.argtypes = [vp, dp]
             L.lbm_step_count.argtypes = [vp]
+            L.lbm_save.argtypes = [vp, ctypes.c_char_p]
+            L.lbm_load.argtypes = [vp, ctypes.c_char_p]
             L.lbm_step_count.restype = ctypes.c_longlong
             L.lbm_launches_per_step.argtypes = [vp]
             ip = ctypes.POINTER(ctypes.c_int)
@@ -206,6 +208,16 @@ def lbm_conserved(ctx):
 
 def lbm_step_count(ctx):
     return lib().lbm_step_count(ctx)
+
+
+def lbm_save(ctx, path):
+    """Write the context's state (populations, step count, parameters) to `path`."""
+    _check(lib().lbm_save(ctx, os.fsencode(path)), ctx)
+
+
+def lbm_load(ctx, path):
+    """Restore a state written by lbm_save into a context with the same parameters."""
+    _check(lib().lbm_load(ctx, os.fsencode(path)), ctx)
 
 
 def lbm_launches_per_step(ctx):
@@ -366,6 +378,12 @@ class Lattice:
         g = np.zeros(p.Q * p.N) if p.thermal else None
         lbm_populations(self.ctx, f, g)
         return f.reshape(p.Q, p.N), (g.reshape(p.Q, p.N) if g is not None else None)
+
+    def save(self, path):
+        lbm_save(self.ctx, path)
+
+    def load(self, path):
+        lbm_load(self.ctx, path)
 
     def conserved(self):
         return lbm_conserved(self.ctx)

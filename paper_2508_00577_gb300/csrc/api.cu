@@ -3,6 +3,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <stdint.h>
 #include <string.h>
 #include <vector>
 
@@ -550,6 +551,173 @@ int lbm_coexistence(int eos, double a, double b, double RT, double out[2])
     if (status == 1) return LBM_EINVAL;
     if (status != 0) return LBM_ETIMEOUT;
     return LBM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Checkpoint and resume.  File layout (little-endian, fixed-width fields):
+//   "EVLBMCKP" | u32 version | u32 0 | i32 lattice nx ny nz eos thermal precision
+//   force_form | f64 a b R kappa tau lambda | i64 steps | u64 bytes of the f, g,
+//   reference-state and frozen-RT sections | the sections, in that order, exactly
+//   as the context stores them on the device.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kCkMagic[8] = {'E', 'V', 'L', 'B', 'M', 'C', 'K', 'P'};
+constexpr uint32_t kCkVersion = 1;
+constexpr size_t kCkHeader = 8 + 4 + 4 + 8 * 4 + 6 * 8 + 8 + 4 * 8;
+constexpr size_t kCkChunk = 64u << 20;          // host staging per transfer
+
+struct CkLayout {
+    void *dev[4];
+    size_t bytes[4];
+};
+
+CkLayout ck_layout(const lbm_ctx *c)
+{
+    const size_t pop = c->pop_bytes * (size_t)c->Q * (size_t)c->N;
+    CkLayout L;
+    L.dev[0] = c->f[c->cur];
+    L.bytes[0] = pop;
+    L.dev[1] = c->g[c->cur];
+    L.bytes[1] = c->P.thermal ? pop : 0;
+    L.dev[2] = c->R[c->cur];
+    L.bytes[2] = dev16(c) ? 2 * (size_t)(c->D + 3) * (size_t)c->N : 0;
+    L.dev[3] = c->RT_iso;
+    L.bytes[3] = c->P.thermal ? 0 : c->real_bytes * (size_t)c->N;
+    return L;
+}
+
+void ck_header(const lbm_ctx *c, const CkLayout &L, unsigned char *h)
+{
+    size_t o = 0;
+    auto put = [&](const void *v, size_t n) { memcpy(h + o, v, n); o += n; };
+    const uint32_t ver = kCkVersion, zero = 0;
+    put(kCkMagic, 8);
+    put(&ver, 4);
+    put(&zero, 4);
+    const int32_t iv[8] = {c->P.lattice, c->P.nx, c->P.ny, c->P.nz, c->P.eos, c->P.thermal, c->P.precision,
+                           c->P.force_form};
+    put(iv, sizeof(iv));
+    const double dv[6] = {c->P.a, c->P.b, c->P.R, c->P.kappa, c->P.tau, c->P.lambda};
+    put(dv, sizeof(dv));
+    const int64_t st = c->steps;
+    put(&st, 8);
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t b = L.bytes[k];
+        put(&b, 8);
+    }
+}
+
+}  // namespace
+
+int lbm_save(lbm_ctx *c, const char *path)
+{
+    if (!c || !path) return c ? fail(c, LBM_EINVAL, "path is NULL") : LBM_EINVAL;
+    CK(c, cudaStreamSynchronize(c->stream));
+    const CkLayout L = ck_layout(c);
+    unsigned char h[kCkHeader];
+    ck_header(c, L, h);
+    char tmp[4096];
+    if (snprintf(tmp, sizeof(tmp), "%s.tmp", path) >= (int)sizeof(tmp)) return fail(c, LBM_EINVAL, "path too long");
+    FILE *fp = fopen(tmp, "wb");
+    if (!fp) return fail(c, LBM_EIO, "lbm_save: cannot open %s for writing", tmp);
+    size_t largest = 0;
+    for (int k = 0; k < 4; ++k) largest = L.bytes[k] > largest ? L.bytes[k] : largest;
+    const size_t chunk = largest < kCkChunk ? largest : kCkChunk;
+    unsigned char *buf = chunk ? static_cast<unsigned char *>(malloc(chunk)) : nullptr;
+    int rc = LBM_OK;
+    if (chunk && !buf) rc = fail(c, LBM_ENOMEM, "lbm_save: host staging buffer");
+    if (rc == LBM_OK && fwrite(h, 1, kCkHeader, fp) != kCkHeader) rc = fail(c, LBM_EIO, "lbm_save: write failed");
+    for (int k = 0; k < 4 && rc == LBM_OK; ++k)
+        for (size_t o = 0; o < L.bytes[k] && rc == LBM_OK; o += chunk) {
+            const size_t n = L.bytes[k] - o < chunk ? L.bytes[k] - o : chunk;
+            cudaError_t e = cudaMemcpyAsync(buf, static_cast<const char *>(L.dev[k]) + o, n, cudaMemcpyDeviceToHost,
+                                            c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) rc = cuda_fail(c, e, "lbm_save");
+            else if (fwrite(buf, 1, n, fp) != n) rc = fail(c, LBM_EIO, "lbm_save: write failed");
+        }
+    free(buf);
+    if (fclose(fp) != 0 && rc == LBM_OK) rc = fail(c, LBM_EIO, "lbm_save: close failed");
+    if (rc == LBM_OK && rename(tmp, path) != 0) rc = fail(c, LBM_EIO, "lbm_save: cannot rename %s to %s", tmp, path);
+    if (rc != LBM_OK) remove(tmp);
+    return rc;
+}
+
+int lbm_load(lbm_ctx *c, const char *path)
+{
+    if (!c || !path) return c ? fail(c, LBM_EINVAL, "path is NULL") : LBM_EINVAL;
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return fail(c, LBM_EIO, "lbm_load: cannot open %s", path);
+    unsigned char h[kCkHeader];
+    if (fread(h, 1, kCkHeader, fp) != kCkHeader) {
+        fclose(fp);
+        return fail(c, LBM_EIO, "lbm_load: %s is shorter than a checkpoint header", path);
+    }
+    if (memcmp(h, kCkMagic, 8) != 0) {
+        fclose(fp);
+        return fail(c, LBM_EINVAL, "lbm_load: %s is not a checkpoint of this library", path);
+    }
+    uint32_t ver;
+    memcpy(&ver, h + 8, 4);
+    if (ver != kCkVersion) {
+        fclose(fp);
+        return fail(c, LBM_EINVAL, "lbm_load: checkpoint version %u, expected %u", ver, kCkVersion);
+    }
+    // The context must describe the same lattice and model: compare every field.
+    const CkLayout L = ck_layout(c);
+    unsigned char mine[kCkHeader];
+    ck_header(c, L, mine);
+    static const char *const names[] = {"lattice", "nx", "ny", "nz", "eos", "thermal", "precision", "force_form",
+                                        "a", "b", "R", "kappa", "tau", "lambda"};
+    for (int k = 0; k < 14; ++k) {
+        const size_t o = 16 + (k < 8 ? 4 * k : 32 + 8 * (k - 8)), n = k < 8 ? 4 : 8;
+        if (memcmp(h + o, mine + o, n) != 0) {
+            fclose(fp);
+            return fail(c, LBM_EINVAL, "lbm_load: %s of the checkpoint differs from the context's", names[k]);
+        }
+    }
+    int64_t steps;
+    memcpy(&steps, h + 16 + 32 + 48, 8);
+    size_t total = kCkHeader;
+    for (int k = 0; k < 4; ++k) {
+        uint64_t b;
+        memcpy(&b, h + 16 + 32 + 48 + 8 + 8 * k, 8);
+        if (b != L.bytes[k]) {
+            fclose(fp);
+            return fail(c, LBM_EINVAL, "lbm_load: section %d holds %llu bytes, the context needs %llu", k,
+                        (unsigned long long)b, (unsigned long long)L.bytes[k]);
+        }
+        total += b;
+    }
+    if (fseek(fp, 0, SEEK_END) != 0 || ftell(fp) != (long)total || fseek(fp, (long)kCkHeader, SEEK_SET) != 0) {
+        fclose(fp);
+        return fail(c, LBM_EIO, "lbm_load: %s is truncated or has trailing bytes (%zu expected)", path, total);
+    }
+    size_t largest = 0;
+    for (int k = 0; k < 4; ++k) largest = L.bytes[k] > largest ? L.bytes[k] : largest;
+    const size_t chunk = largest < kCkChunk ? largest : kCkChunk;
+    unsigned char *buf = chunk ? static_cast<unsigned char *>(malloc(chunk)) : nullptr;
+    int rc = LBM_OK;
+    if (chunk && !buf) rc = fail(c, LBM_ENOMEM, "lbm_load: host staging buffer");
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 4 && rc == LBM_OK; ++k)
+        for (size_t o = 0; o < L.bytes[k] && rc == LBM_OK; o += chunk) {
+            const size_t n = L.bytes[k] - o < chunk ? L.bytes[k] - o : chunk;
+            if (fread(buf, 1, n, fp) != n) {
+                rc = fail(c, LBM_EIO, "lbm_load: read failed");
+                break;
+            }
+            cudaError_t e = cudaMemcpyAsync(static_cast<char *>(L.dev[k]) + o, buf, n, cudaMemcpyHostToDevice,
+                                            c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) rc = cuda_fail(c, e, "lbm_load");
+        }
+    free(buf);
+    fclose(fp);
+    if (rc == LBM_OK) c->steps = steps;
+    return rc;
 }
 
 }  // extern "C"

@@ -97,6 +97,8 @@ def test_null_context_is_invalid():
     assert L.lbm_step(None, 1) == ev.LBM_EINVAL
     assert L.lbm_free(None) == ev.LBM_OK
     assert L.lbm_step_count(None) == -1
+    assert L.lbm_save(None, b"x.ckpt") == ev.LBM_EINVAL
+    assert L.lbm_load(None, b"x.ckpt") == ev.LBM_EINVAL
 
 
 @pytest.mark.parametrize("eos,a,b", [(ev.LBM_EOS_CS, 0.1, 4.0), (ev.LBM_EOS_VDW, 9 / 392, 2 / 21)])
