@@ -348,7 +348,10 @@ def run_ensemble(args):
     value = N * args.steps / (ms * 1e-3) / 1e6
     peak, peak_kind = peaks()
     achieved = BYTES_PER_LU * N * args.steps / (ms * 1e-3) / 1e9
-    finite = all(np.isfinite(bt.moments(d)[0]).all() for d in (0, len(sizes) // 2, len(sizes) - 1))
+    # Every domain is checked: a few coalescing pairs near T/Tc = 0.7 leave the method's
+    # stability range within a few hundred steps (the FP64 oracle diverges on them too);
+    # their NaN arithmetic costs the same on the GPU, and the count is reported.
+    n_finite = sum(bool(np.isfinite(bt.moments(d)[0]).all()) for d in range(len(sizes)))
     bt.close()
     return {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -359,7 +362,8 @@ def run_ensemble(args):
                    "nodes": N, "tile": {"w": tile[0], "h": tile[1], "autotuned": True}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "note": f"{BYTES_PER_LU} algorithmic B/LU; peak {peak_kind}"},
-        "clocks": clk.summary(), "gpu_launches": 1, "finite": bool(finite),
+        "clocks": clk.summary(), "gpu_launches": 1, "finite": n_finite == len(sizes),
+        "finite_domains": f"{n_finite}/{len(sizes)}",
     }
 
 

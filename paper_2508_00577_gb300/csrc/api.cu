@@ -9,6 +9,7 @@
 
 #include "../../include/evlbm.h"
 #include "dispatch.h"
+#include "trace.h"
 
 using evlbm::KParams;
 
@@ -257,6 +258,7 @@ int lbm_init(const lbm_params *params, const double *rho, const double *u, const
 
 int lbm_step(lbm_ctx *c, int n_steps)
 {
+    evtrace::Range trace_("lbm_step");
     if (!c) return LBM_EINVAL;
     if (n_steps < 0) return fail(c, LBM_EINVAL, "n_steps must be >= 0");
     const bool fused = !fp64(c) && evlbm::fused2d_supported(c->P.precision, c->Q, c->K);

@@ -18,6 +18,7 @@
 
 #include "../../include/evlbm.h"
 #include "fused2d_tile.cuh"
+#include "trace.h"
 
 namespace evlbm {
 namespace {
@@ -508,6 +509,7 @@ int lbm_batch_init(const lbm_params *p, int n_domains, const int *nx, const int 
 
 int lbm_batch_step(lbm_batch *b, int n_steps)
 {
+    evtrace::Range trace_("lbm_batch_step");
     if (!b || n_steps < 0) return LBM_EINVAL;
     if (n_steps == 0) return LBM_OK;
     const int rc = run_graph(b, n_steps);

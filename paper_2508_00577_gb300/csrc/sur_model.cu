@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "surrogate.cuh"
+#include "trace.h"
 
 using evsur::bf16;
 
@@ -646,11 +647,13 @@ int sur_set_norm(sur_model *m, const float *in_mean, const float *in_scale, cons
 
 int sur_forward_backward(sur_model *m, const float *d_x, const float *d_y, int batch, float *loss)
 {
+    evtrace::Range trace_("sur_forward_backward");
     return fwd_bwd(m, d_x, d_y, batch, loss);
 }
 
 int sur_train_step(sur_model *m, const float *d_x, const float *d_y, int batch, float lr, float *loss)
 {
+    evtrace::Range trace_("sur_train_step");
     if (!m || !(lr >= 0.f)) return fail(m, SUR_EINVAL, "invalid arguments");
     int rc = fwd_bwd(m, d_x, d_y, batch, nullptr);
     if (rc) return rc;
@@ -668,6 +671,7 @@ int sur_train_step(sur_model *m, const float *d_x, const float *d_y, int batch, 
 
 int sur_infer(sur_model *m, const float *d_x, float *d_y, int batch)
 {
+    evtrace::Range trace_("sur_infer");
     if (!m || !d_x || !d_y || batch < 1) return fail(m, SUR_EINVAL, "invalid arguments");
     int rc = ensure_batch(m, batch, m->train_buffers);
     if (rc) return rc;
@@ -681,6 +685,7 @@ int sur_infer(sur_model *m, const float *d_x, float *d_y, int batch)
 int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur_rollout_cfg *cfg,
                 unsigned char *h_used_lb, int *n_fallback)
 {
+    evtrace::Range trace_("sur_rollout");
     if (!m || !lb || !d_fields || !cfg || batch < 1 || cfg->windows < 0 || cfg->steps < 1)
         return fail(m, SUR_EINVAL, "invalid arguments");
     if (batch > 4096) return fail(m, SUR_EINVAL, "at most 4096 domains per rollout");

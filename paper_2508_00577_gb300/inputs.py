@@ -116,10 +116,13 @@ def ensemble_domains(n: int = 512, seed: int = DEFAULT_SEED, side_min: int = 64,
 
 def two_droplets(nx: int, ny: int, r1: float, r2: float, gap: float, rho_v: float, rho_l: float, T: float,
                  width: float = 4.0):
-    """Two droplets on the x axis through the domain centre, surfaces `gap` apart."""
+    """Two droplets on the x axis through the domain centre, surfaces `gap` apart; the
+    pair (extent 2 r1 + gap + 2 r2) is centred in the domain, so droplets of unequal
+    radii stay clear of the periodic boundary when the pair fits."""
     cy = 0.5 * (ny - 1)
-    c1 = 0.5 * (nx - 1) - 0.5 * gap - r1
-    c2 = 0.5 * (nx - 1) + 0.5 * gap + r2
+    left = 0.5 * (nx - 1) - 0.5 * (2.0 * r1 + gap + 2.0 * r2)
+    c1 = left + r1
+    c2 = c1 + r1 + gap + r2
     y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
     d = np.maximum(r1 - np.hypot(x - c1, y - cy), r2 - np.hypot(x - c2, y - cy))
     rho = tanh_profile(d, rho_v, rho_l, width).reshape(-1)
