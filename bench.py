@@ -569,7 +569,11 @@ def run_spinodal3d(args):
                                tau=TAU, precision=prec)
         stream = torch.cuda.Stream()
         with ev.Lattice(p, rho, u, T, stream=stream.cuda_stream) as g:
-            tile = ev.lbm_autotune(g.ctx, 2)         # z-chunk of the fused FP32 kernel; no-op otherwise
+            if args.tile and prec == ev.LBM_FP32:    # fixed 16 x H (z-chunk) launch shape
+                tile = tuple(int(v) for v in args.tile.split(","))
+                ev.lbm_set_tile(g.ctx, *tile)
+            else:
+                tile = ev.lbm_autotune(g.ctx, 2)     # z-chunk of the fused FP32 kernel; no-op otherwise
             g.step(args.warmup)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
