@@ -132,6 +132,15 @@ int lbm_conserved(lbm_ctx *ctx, double out[5]);
 /* Number of time steps taken since lbm_init. */
 long long lbm_step_count(const lbm_ctx *ctx);
 
+/* Diagnostic, no counterpart in the paper: the number of out-of-range global or
+ * shared-memory indices the fused kernels (D2Q9, D3Q27, batched ensemble) have met
+ * since the library was loaded, in a library built with bounds checking
+ * (libevlbm_bc.so, compiled with -DEVLBM_BOUNDS_CHECK; such an access is skipped and
+ * counted, never performed, and nothing traps).  Returns -1 from a library built
+ * without the checks and -2 if reading the device counters failed.  Stands in for a
+ * memory checker on machines where none can be run. */
+long long lbm_bounds_violations(void);
+
 /* Checkpoint and resume.  The method has no state beyond the post-collision
  * populations of Eq. (pre_LBM) (plus, per storage type, the per-node reference
  * states of 16-bit deviation storage and the frozen R T field when thermal = 0),

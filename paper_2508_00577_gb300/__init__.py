@@ -19,7 +19,7 @@ __all__ = [
     "lbm_populations", "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_set_tile",
     "lbm_get_tile", "lbm_autotune", "lbm_sync", "lbm_free",
     "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "lbm_step_noalloc", "lbm_reset_device",
-    "lbm_save", "lbm_load", "LBMError", "Lattice",
+    "lbm_save", "lbm_load", "lbm_bounds_violations", "LBMError", "Lattice",
     "LBM_D2Q9", "LBM_D3Q27", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
     "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS", "Batch",
 ]
@@ -40,6 +40,7 @@ EXPORTED_SYMBOLS = (
     "lbm_step_noalloc", "lbm_batch_init", "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_tile",
     "lbm_batch_get_tile", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_batch_nodes",
     "lbm_batch_free", "lbm_batch_last_error", "lbm_reset_device", "lbm_save", "lbm_load",
+    "lbm_bounds_violations",
 )
 
 
@@ -85,9 +86,11 @@ def lib():
     with _lock:
         if _lib is None:
             from . import _build
-            path = _build.LIB
-            if not os.path.exists(path) or _build_needed(_build):
-                _build.build()
+            path = os.environ.get("EVLBM_LIBRARY", "")
+            if not path:                      # the in-tree library, rebuilt when stale
+                path = _build.LIB
+                if not os.path.exists(path) or _build_needed(_build):
+                    _build.build()
             L = ctypes.CDLL(path)
             dp = ctypes.POINTER(ctypes.c_double)
             pp = ctypes.POINTER(lbm_params)
@@ -100,6 +103,8 @@ def lib():
             L.lbm_populations.argtypes = [vp, dp, dp]
             L.lbm_conserved.argtypes = [vp, dp]
             L.lbm_step_count.argtypes = [vp]
+            L.lbm_bounds_violations.argtypes = []
+            L.lbm_bounds_violations.restype = ctypes.c_longlong
             L.lbm_save.argtypes = [vp, ctypes.c_char_p]
             L.lbm_load.argtypes = [vp, ctypes.c_char_p]
             L.lbm_step_count.restype = ctypes.c_longlong
@@ -208,6 +213,11 @@ def lbm_conserved(ctx):
 
 def lbm_step_count(ctx):
     return lib().lbm_step_count(ctx)
+
+
+def lbm_bounds_violations():
+    """Out-of-range indices met by the fused kernels of a bounds-checked library (-1: no checks)."""
+    return lib().lbm_bounds_violations()
 
 
 def lbm_save(ctx, path):

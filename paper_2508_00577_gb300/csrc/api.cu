@@ -371,6 +371,17 @@ int lbm_conserved(lbm_ctx *c, double out[5])
 
 long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
 
+long long lbm_bounds_violations(void)
+{
+    const long long v[3] = {evlbm::fused2d_oob(), evlbm::fused3d_oob(), evlbm::batch_oob()};
+    long long total = 0;
+    for (long long x : v) {
+        if (x < 0) return x;
+        total += x;
+    }
+    return total;
+}
+
 int lbm_launches_per_step(const lbm_ctx *c)
 {
     if (!c) return -1;

@@ -189,6 +189,9 @@ int grid_for(int W)
 }
 
 }  // namespace
+
+EVLBM_DEFINE_OOB_READER(batch_oob)
+
 }  // namespace evlbm
 
 using evlbm::BatchArgs;

@@ -63,4 +63,11 @@ cudaError_t totals(int prec, int Q, const KParams &p, const void *f, const void 
 // Maxwell construction in FP64 on the GPU.
 cudaError_t coexistence(int eos, double a, double b, double RT, double rho_c, double *h_out, int *h_status);
 
+// Out-of-range accesses counted by the fused kernels of a bounds-checked build
+// (-DEVLBM_BOUNDS_CHECK): the count, -1 when the library was built without the
+// checks, -2 on a CUDA error.
+long long fused2d_oob();
+long long fused3d_oob();
+long long batch_oob();
+
 }  // namespace evlbm

@@ -44,6 +44,8 @@ cudaError_t launch(int W, const FusedArgs &A, int nz, cudaStream_t st)
 
 }  // namespace
 
+EVLBM_DEFINE_OOB_READER(fused2d_oob)
+
 const int kFusedWidths[kFusedWidthCount] = {64, 96, 128, 192};
 
 bool fused2d_supported(int prec, int Q, const KParams &p)

@@ -33,6 +33,7 @@
 // served by L2.
 #pragma once
 
+#include "bounds.cuh"
 #include "dispatch.h"
 
 namespace evlbm {
@@ -115,7 +116,8 @@ __device__ __forceinline__ void pull18(const float *__restrict__ base, unsigned 
     for (int i = 0; i < 9; ++i) {
         const int cx = i % 3 - 1, cy = i / 3 - 1;
         const float *p = base + i * N + cols[1 - cx];
-        h[i] = V(ldpop<CG>(p + ro[1 - cy]), ldpop<CG>(p + ro[2 - cy]));
+        const float *p0 = p + ro[1 - cy], *p1 = p + ro[2 - cy];
+        h[i] = V(in_bounds(p0 - base, 9ull * N) ? ldpop<CG>(p0) : 0.f, in_bounds(p1 - base, 9ull * N) ? ldpop<CG>(p1) : 0.f);
     }
 }
 
@@ -172,6 +174,11 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
     int cols[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) cols[k] = wrap_any(col - 1 + k, nx);
+    // Shared rings: stages B and C read slot +- 1, stage D the thread-private rings at t.
+    // A thread that fails the check does no work but still reaches every barrier.
+    if (!in_bounds(slot, S) || ((inB || inC) && !(in_bounds(slot - 1, S) && in_bounds(slot + 1, S))) ||
+        (inD && !in_bounds(t, kW)))
+        inA = inB = inC = inD = false;
 
     const float a = A.a, b = A.b, kappa = A.kappa, lambda = A.lambda;
     const unsigned N = A.N;
@@ -292,7 +299,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
                 }
             } else {
                 const float *Tp = A.RT_iso + layer + cols[1];
-                RT = V(ldpop<CG>(Tp + (unsigned)rC * nx), ldpop<CG>(Tp + (unsigned)next_row(rC, ny) * nx));
+                const float *T0 = Tp + (unsigned)rC * nx, *T1 = Tp + (unsigned)next_row(rC, ny) * nx;
+                RT = V(in_bounds(T0 - A.RT_iso, N) ? ldpop<CG>(T0) : 0.f, in_bounds(T1 - A.RT_iso, N) ? ldpop<CG>(T1) : 0.f);
                 rC = next_row(next_row(rC, ny), ny);
             }
             // EOS in the Enskog gauge: P0 = P_E = rho RT Z, gamma0 = 1 + rho Z'/Z [+ 2/3 Z].
@@ -381,8 +389,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
             for (int i = 0; i < 9; ++i) {
                 const int ix = i % 3, iy = i / 3;
                 const v2 o = fma2(kh, fr[i * kW], fma2(exk[ix], ey[iy], sxk[ix] * sy[iy]));
-                A.fo[i * N + out0] = o.x;
-                if (second) A.fo[i * N + out1] = o.y;
+                if (in_bounds(i * N + out0, 9ull * N)) A.fo[i * N + out0] = o.x;
+                if (second && in_bounds(i * N + out1, 9ull * N)) A.fo[i * N + out1] = o.y;
             }
             if constexpr (THERMAL) {
                 // g^eq_i = rho [e PsiP_x PsiP_y + PsiS_x PsiP_y + PsiP_x PsiS_y], e = 3/2 RT,
@@ -424,8 +432,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
                     if (i == 7) c = c + hqy;   // c = (0,1)
                     c = fma2(exk[ix], Sy[iy], fma2(Ax[ix], ey[iy], c));      // + keq g^eq
                     const v2 o = fma2(kh, gr[i * kW], c);
-                    A.go[i * N + out0] = o.x;
-                    if (second) A.go[i * N + out1] = o.y;
+                    if (in_bounds(i * N + out0, 9ull * N)) A.go[i * N + out0] = o.x;
+                    if (second && in_bounds(i * N + out1, 9ull * N)) A.go[i * N + out1] = o.y;
                 }
             }
             rD = next_row(next_row(rD, ny), ny);

@@ -20,6 +20,7 @@
 // centre values pass from C to D through a one-plane per-thread slot (stage C takes
 // the tile column a thread collides in D first, and reads the slot before rewriting
 // it); at 80.7 KB per CTA two CTAs leave the L1 ~92 KB for loads in flight.
+#include "bounds.cuh"
 #include "dispatch.h"
 
 namespace evlbm {
@@ -56,6 +57,16 @@ __device__ __forceinline__ float rcpa(float a)
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
     return r;
+}
+
+// Global loads and stores with the bounds check of checked builds (no-op otherwise).
+__device__ __forceinline__ float ldc(const float *base, unsigned off, unsigned long long n)
+{
+    return in_bounds(off, n) ? __ldg(base + off) : 0.f;
+}
+__device__ __forceinline__ void stc(float *base, unsigned off, unsigned long long n, float v)
+{
+    if (in_bounds(off, n)) __stcs(base + off, v);
 }
 
 __device__ __forceinline__ int wrapi(int v, int n)
@@ -167,14 +178,14 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                 float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
                 for (int i = 0; i < 27; ++i) {
-                    const float h = __ldg(A.f + src_of(i, c, zo, N));
+                    const float h = ldc(A.f, src_of(i, c, zo, N), 27ull * N);
                     rho += h;
                     if (cxi(i) == 1) jx += h; else if (cxi(i) == -1) jx -= h;
                     if (cyi(i) == 1) jy += h; else if (cyi(i) == -1) jy -= h;
                     if (czi(i) == 1) jz += h; else if (czi(i) == -1) jz -= h;
                 }
-                RHO[s0 * SA + sa(cx, cy)] = rho;
-                if (cx >= -1 && cx <= TX && cy >= -1 && cy <= TY) {
+                if (in_bounds(sa(cx, cy), SA)) RHO[s0 * SA + sa(cx, cy)] = rho;
+                if (cx >= -1 && cx <= TX && cy >= -1 && cy <= TY && in_bounds(sc(cx, cy), SC)) {
                     float *jr = J + s0 * 3 * SC + sc(cx, cy);
                     jr[0] = jx;
                     jr[SC] = jy;
@@ -192,6 +203,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                 if (!colB(k, cx, cy)) continue;
                 const float *r[3] = {RHO + sm2 * SA, RHO + sm1 * SA, RHO + s0 * SA};   // planes q-2, q-1, q
                 const int c0 = sa(cx, cy);
+                if (!(in_bounds(c0 - WA - 1, SA) && in_bounds(c0 + WA + 1, SA) && in_bounds(sb(cx, cy), SB))) continue;
                 const float rc = r[1][c0];
                 float gx = 0.f, gy = 0.f, gz = 0.f, lap = 0.f;
 #pragma unroll
@@ -230,6 +242,9 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                 // Pi of planes q-3 (slot s0), q-2 (sm2), q-1 (sm1).
                 const float *P[3] = {PI + s0 * 6 * SB, PI + sm2 * 6 * SB, PI + sm1 * 6 * SB};
                 const int b0 = sb(cx, cy);
+                if (!(in_bounds(b0 - WB - 1, SB) && in_bounds(b0 + WB + 1, SB) && in_bounds(sc(cx, cy), SC) &&
+                      in_bounds(sa(cx, cy), SA)))
+                    continue;
                 // d_b Pi_ab with the isotropic gradient 3 sum_i w_i c_ib Pi_ab(x + c_i).
                 float dPi[6][3];                          // [component][direction]
 #pragma unroll
@@ -271,13 +286,13 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                     const Cell c = cell_of(x0 + cx, y0 + cy, nx, ny);
                     float Gam = 0.f;
 #pragma unroll
-                    for (int i = 0; i < 27; ++i) Gam += __ldg(A.g + src_of(i, c, zo, N));
+                    for (int i = 0; i < 27; ++i) Gam += ldc(A.g, src_of(i, c, zo, N), 27ull * N);
                     const float E = (Gam + 0.5f * (ux * Fx + uy * Fy + uz * Fz)) * ir;
                     RT = (2.f / 3.f) * (E - 0.5f * (ux * ux + uy * uy + uz * uz));
                 } else {
                     const unsigned n = (unsigned)zc * (unsigned)nx * (unsigned)ny +
                                        (unsigned)wrapi(y0 + cy, ny) * (unsigned)nx + (unsigned)wrapi(x0 + cx, nx);
-                    RT = __ldg(A.RT_iso + n);
+                    RT = ldc(A.RT_iso, n, N);
                 }
                 // EOS in the Enskog gauge: P0 = P_E = rho RT Z, gamma0 = 1 + rho Z'/Z [+ 2/3 Z].
                 float Z, dlnZ;
@@ -317,7 +332,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
 
         // ---------------- D: collide plane q-3 ----------------
         const int p = q - 3;
-        if (p >= z0 && p < zend && inD) {
+        if (p >= z0 && p < zend && inD && in_bounds(sc(dcx, dcy) - WC, SC) && in_bounds(sc(dcx, dcy) + WC, SC)) {
             // Centre values of plane p (stage C ran at iteration q-1), read in stage C.
             const float rho = cprev[0], Fx = cprev[1], Fy = cprev[2], Fz = cprev[3];
             const float RT = cprev[4], th = cprev[5], g0 = cprev[6];
@@ -373,8 +388,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                 const int ix = cxi(i) + 1, iyz = 3 * (cyi(i) + 1) + czi(i) + 1;
                 // The output is not read again this step: a streaming store keeps L2 for
                 // the populations the stages still share.
-                const float h = __ldg(A.f + src_of(i, cD, zo, N));
-                __stcs(A.fo + (unsigned)i * N + out, kh * h + keq * (rex[ix] * Eyz[iyz]) + kst * (rsx[ix] * Syz[iyz]));
+                const float h = ldc(A.f, src_of(i, cD, zo, N), 27ull * N);
+                stc(A.fo, (unsigned)i * N + out, 27ull * N, kh * h + keq * (rex[ix] * Eyz[iyz]) + kst * (rsx[ix] * Syz[iyz]));
             }
             if (THERMAL) {
                 // g^eq_i = rho [e PP_x PP_y PP_z + PS_x PP_y PP_z + PP_x PS_y PP_z + PP_x PP_y PS_z]
@@ -418,13 +433,13 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
 #pragma unroll
                 for (int i = 0; i < 27; ++i) {
                     const int ix = cxi(i) + 1, iyz = 3 * (cyi(i) + 1) + czi(i) + 1;
-                    const float h = __ldg(A.g + src_of(i, cD, zo, N));
+                    const float h = ldc(A.g, src_of(i, cD, zo, N), 27ull * N);
                     const float geq = Ag[ix] * Eyz[iyz] + rex[ix] * Cyz[iyz];
                     float gst = As[ix] * Pyz[iyz] + rpx[ix] * Dyz[iyz];
                     if (abs(cxi(i)) + abs(cyi(i)) + abs(czi(i)) == 1)
                         gst += (cxi(i) ? cxi(i) * hq[0] : 0.f) + (cyi(i) ? cyi(i) * hq[1] : 0.f) +
                                (czi(i) ? czi(i) * hq[2] : 0.f);
-                    __stcs(A.go + (unsigned)i * N + out, kh * h + keq * geq + kst * gst);
+                    stc(A.go, (unsigned)i * N + out, 27ull * N, kh * h + keq * geq + kst * gst);
                 }
             }
         }
@@ -449,6 +464,8 @@ cudaError_t launch(const Args &A, cudaStream_t st)
 }
 
 }  // namespace
+
+EVLBM_DEFINE_OOB_READER(fused3d_oob)
 
 bool fused3d_supported(int prec, int Q, const KParams &p)
 {

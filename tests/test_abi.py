@@ -92,6 +92,18 @@ def test_nonpositive_fields_rejected_on_host():
     assert "node 5" in ev.lbm_last_error(None)
 
 
+def test_bounds_check_query():
+    """The default library has no bounds checks (-1); the checked variant, when built,
+    loads and exports every declared symbol."""
+    assert ev.lib().lbm_bounds_violations() == -1
+    from paper_2508_00577_gb300 import _build
+    if not os.path.exists(_build.LIB_BC):
+        pytest.skip("bounds-checked library not built")
+    L = ctypes.CDLL(_build.LIB_BC)
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
 def test_null_context_is_invalid():
     L = ev.lib()
     assert L.lbm_step(None, 1) == ev.LBM_EINVAL
