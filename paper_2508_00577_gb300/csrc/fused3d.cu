@@ -34,8 +34,9 @@ constexpr int SA = WA * WA, SB = WB * WB, SC = WC * WC;
 // Shared-memory layout (floats).
 constexpr int O_RHO = 0;                          // [3][SA]
 constexpr int O_J = O_RHO + 3 * SA;               // [3 planes][3 comps][SC]
-constexpr int O_PI = O_J + 9 * SC;                // [3 planes][6 comps][SB]  xx xy xz yy yz zz
-constexpr int O_CF = O_PI + 18 * SB;              // [3 planes][7][SC]  ux uy uz qx qy qz wq
+constexpr int O_PI = O_J + 9 * SC;                // [6 comps][SB]  xx xy xz yy yz zz of the newest plane
+constexpr int O_PF = O_PI + 6 * SB;               // [3 planes][3 comps][SC]  partial forces, per stage-C column
+constexpr int O_CF = O_PF + 9 * SC;               // [3 planes][7][SC]  ux uy uz qx qy qz wq
 constexpr int O_CEN = O_CF + 21 * SC;             // [7][NT]  rho Fx Fy Fz RT theta0 gamma0 (one plane)
 constexpr int SMEM_FLOATS = O_CEN + 7 * NT;
 constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
     auto sa = [](int cx, int cy) { return (cy + 3) * WA + (cx + 3); };
     auto sb = [](int cx, int cy) { return (cy + 2) * WB + (cx + 2); };
     auto sc = [](int cx, int cy) { return (cy + 1) * WC + (cx + 1); };
-    float *RHO = sm + O_RHO, *J = sm + O_J, *PI = sm + O_PI, *CF = sm + O_CF, *CEN = sm + O_CEN;
+    float *RHO = sm + O_RHO, *J = sm + O_J, *PI = sm + O_PI, *PF = sm + O_PF, *CF = sm + O_CF, *CEN = sm + O_CEN;
 
     const int dcx = t % TX, dcy = t / TX;                 // this thread's output column
     const bool inD = x0 + dcx < nx && y0 + dcy < ny;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                 }
                 gx *= 3.f; gy *= 3.f; gz *= 3.f; lap *= 6.f;
                 const float s = -a * rc * rc - kappa * rc * lap - 0.5f * kappa * (gx * gx + gy * gy + gz * gz);
-                float *pr = PI + sm1 * 6 * SB + sb(cx, cy);
+                float *pr = PI + sb(cx, cy);
                 pr[0] = s + kappa * gx * gx;
                 pr[SB] = kappa * gx * gy;
                 pr[2 * SB] = kappa * gx * gz;
@@ -230,53 +231,62 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
         __syncthreads();
 
         // ---------------- C: F, u, T, EOS of plane q-2 ----------------
+        // The force F_a = -d_b Pi_ab = -3 sum_i w_i c_ib Pi_ab(x + c_i) splits by plane: the
+        // stress plane P adds w1(cz) (T_a + cz S_a) to the force of plane P - cz, with the
+        // in-plane sums T_a = sum w1(cx) w1(cy) (cx Pi_ax + cy Pi_ay) and
+        // S_a = sum w1(cx) w1(cy) Pi_az over the 3 x 3 neighbours (w_i = w1(cx) w1(cy) w1(cz),
+        // w1(0) = 2/3, w1(+-1) = 1/6).  Each new stress plane (q-1, from stage B) is folded
+        // into the partial forces of planes q (first term), q-1 and q-2 (complete), kept
+        // per stage-C column (thread-private).
         float cprev[7];                                   // centre values of plane q-3 (stage D)
-        if (q - 2 >= z0 - 1 && q - 2 <= zend) {
+        const bool haveP = q - 1 >= z0 - 2 && q - 1 <= zend + 1;   // stage B wrote Pi(q-1)
+        if (haveP) {
             unsigned zo[3];
             if (THERMAL) plane_offsets(q - 2, nx, ny, nz, zo);
             const int zc = wrapi(q - 2, nz);
+            const bool runC = q - 2 >= z0 - 1 && q - 2 <= zend;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 int cx, cy;
                 if (!colC(k, cx, cy)) continue;
-                // Pi of planes q-3 (slot s0), q-2 (sm2), q-1 (sm1).
-                const float *P[3] = {PI + s0 * 6 * SB, PI + sm2 * 6 * SB, PI + sm1 * 6 * SB};
                 const int b0 = sb(cx, cy);
+                const int pc = k == 0 ? t : NT + t;       // this column's partial-force slot
                 if (!(in_bounds(b0 - WB - 1, SB) && in_bounds(b0 + WB + 1, SB) && in_bounds(sc(cx, cy), SC) &&
-                      in_bounds(sa(cx, cy), SA)))
+                      in_bounds(sa(cx, cy), SA) && in_bounds(pc, SC)))
                     continue;
-                // d_b Pi_ab with the isotropic gradient 3 sum_i w_i c_ib Pi_ab(x + c_i).
-                float dPi[6][3];                          // [component][direction]
+                float T[3] = {0.f, 0.f, 0.f}, Sz[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-                for (int m = 0; m < 6; ++m) dPi[m][0] = dPi[m][1] = dPi[m][2] = 0.f;
+                for (int oy = -1; oy <= 1; ++oy)
 #pragma unroll
-                for (int i = 0; i < 27; ++i) {
-                    if (i == 13) continue;
-                    const float w = wi(i);
-                    const float *pp = P[1 + czi(i)] + b0 + cyi(i) * WB + cxi(i);
-                    // Components needed: x-derivative of xx, xy, xz; y of xy, yy, yz; z of xz, yz, zz.
-                    if (cxi(i)) {
-                        const float cw = cxi(i) * w;
-                        dPi[0][0] += cw * pp[0];
-                        dPi[1][0] += cw * pp[SB];
-                        dPi[2][0] += cw * pp[2 * SB];
+                    for (int ox = -1; ox <= 1; ++ox) {
+                        const float w = (ox ? 1.f / 6.f : 2.f / 3.f) * (oy ? 1.f / 6.f : 2.f / 3.f);
+                        const float *pp = PI + b0 + oy * WB + ox;
+                        if (ox) {
+                            const float cw = ox * w;
+                            T[0] += cw * pp[0];
+                            T[1] += cw * pp[SB];
+                            T[2] += cw * pp[2 * SB];
+                        }
+                        if (oy) {
+                            const float cw = oy * w;
+                            T[0] += cw * pp[SB];
+                            T[1] += cw * pp[3 * SB];
+                            T[2] += cw * pp[4 * SB];
+                        }
+                        Sz[0] += w * pp[2 * SB];
+                        Sz[1] += w * pp[4 * SB];
+                        Sz[2] += w * pp[5 * SB];
                     }
-                    if (cyi(i)) {
-                        const float cw = cyi(i) * w;
-                        dPi[1][1] += cw * pp[SB];
-                        dPi[3][1] += cw * pp[3 * SB];
-                        dPi[4][1] += cw * pp[4 * SB];
-                    }
-                    if (czi(i)) {
-                        const float cw = czi(i) * w;
-                        dPi[2][2] += cw * pp[2 * SB];
-                        dPi[4][2] += cw * pp[4 * SB];
-                        dPi[5][2] += cw * pp[5 * SB];
-                    }
+                float *fq = PF + s0 * 3 * SC + pc, *fq1 = PF + sm1 * 3 * SC + pc, *fq2 = PF + sm2 * 3 * SC + pc;
+                float F[3];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    fq[m * SC] = (1.f / 6.f) * (T[m] - Sz[m]);           // plane q,   cz = -1 (first term)
+                    fq1[m * SC] += (2.f / 3.f) * T[m];                  // plane q-1, cz = 0
+                    F[m] = -3.f * (fq2[m * SC] + (1.f / 6.f) * (T[m] + Sz[m]));   // plane q-2, complete
                 }
-                const float Fx = -3.f * (dPi[0][0] + dPi[1][1] + dPi[2][2]);
-                const float Fy = -3.f * (dPi[1][0] + dPi[3][1] + dPi[4][2]);
-                const float Fz = -3.f * (dPi[2][0] + dPi[4][1] + dPi[5][2]);
+                if (!runC) continue;
+                const float Fx = F[0], Fy = F[1], Fz = F[2];
                 const float rho = RHO[sm2 * SA + sa(cx, cy)];
                 const float *jr = J + sm2 * 3 * SC + sc(cx, cy);
                 const float ir = rcpa(rho);
