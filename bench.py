@@ -296,7 +296,7 @@ def run(args):
         eargs.domains, eargs.steps, eargs.warmup = 512, 2000, 20
         e_line = run_ensemble(eargs)
         line["ensemble"] = {k: e_line[k] for k in ("metric", "value", "unit", "steps", "ms_per_step", "config",
-                                                     "roofline", "finite")}
+                                                     "roofline", "finite", "finite_domains")}
         sargs3 = argparse.Namespace(**vars(args))
         sargs3.steps, sargs3.warmup = 20, 3
         line["spinodal3d"] = run_spinodal3d(sargs3)
