@@ -422,6 +422,12 @@ struct TArgs {
     int lh, lw;        // interior grid of A
     int boxw, boxh;    // pixels of one box row, box rows (a tile is boxw * boxh * boxs pixels)
     int b_c0;          // first K column of B
+    // MN-major mode (weight gradients: pixels along K, split over K):
+    int a_cb, b_cb;    // channels per box (MN atom): 64 (128-byte swizzle), 32 (64-byte), 8 (none)
+    int a_lbo, a_sbo, a_kstep, a_sw;   // smem descriptor of A: byte offsets, K-step advance, layout
+    int b_lbo, b_sbo, b_kstep, b_sw;
+    int splits;        // K splits (tiles = mtiles x ntiles x splits)
+    long long K, kps;  // reduction length and K per split (multiples of 64)
     Epi e;
 };
 
@@ -461,7 +467,41 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 //   warp 5 (one thread): MMA issuer          empty[s]  <- tcgen05.commit
 //   warps 0-3: epilogue                      tfull[b]  <- tcgen05.commit (accumulator b ready)
 //                                            tempty[b] <- 128 epilogue arrivals (b drained)
-template <int BN, int ASW>
+// Tile of the persistent loop: output block (m0, n0) and its K range.  MN-major mode
+// orders tiles (split, m, n), n fastest, so that tiles over the same pixels run together.
+struct TileCoord {
+    long long m0, kbeg;
+    int n0, nkb;
+};
+
+template <bool MN>
+__device__ __forceinline__ TileCoord tile_coord(const TArgs &g, int tile)
+{
+    TileCoord c;
+    if (MN) {
+        const int per = g.mtiles * g.ntiles, sp = tile / per, rem = tile - sp * per;
+        c.m0 = (long long)(rem / g.ntiles) * BM;
+        c.n0 = rem % g.ntiles;
+        c.kbeg = (long long)sp * g.kps;
+        const long long kend = c.kbeg + g.kps < g.K ? c.kbeg + g.kps : g.K;
+        c.nkb = (int)((kend - c.kbeg) / BK);
+    } else {
+        c.m0 = (long long)(tile / g.ntiles) * BM;
+        c.n0 = tile % g.ntiles;
+        c.kbeg = 0;
+        c.nkb = g.nkb;
+    }
+    return c;
+}
+
+// MN = true: weight-gradient form, A = TCONV3 or TPIX and B = TPIX (pixels along K),
+// both MN-major.  A K block is 64 consecutive pixels (boxw x boxh of one image); each
+// box loads one MN atom of cb channels for those 64 pixels, 64 rows of cb x 2 bytes:
+// with cb = 64 a 128-byte-swizzled atom column (8-row groups 1 KB apart), cb = 32 a
+// 64-byte-swizzled one (512 B), cb = 8 unswizzled core matrices (128 B).  Descriptors:
+// swizzled MN-major layouts take LBO = stride between MN atoms and SBO = stride between
+// 8-row K groups; the unswizzled one LBO = K-group stride and SBO = MN stride.
+template <int BN, int ASW, bool MN>
 __global__ void __launch_bounds__(192, 1)
     k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TArgs g)
 {
@@ -477,7 +517,7 @@ __global__ void __launch_bounds__(192, 1)
     __shared__ int abort_flag;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     volatile int *abort_v = &abort_flag;
-    const int ntiles = g.mtiles * g.ntiles;
+    const int ntiles = g.mtiles * g.ntiles * (MN ? g.splits : 1);
 
     if (warp == 0) tmem_alloc(&tmem_sh, TCOLS);
     if (t == 0) {
@@ -507,6 +547,45 @@ __global__ void __launch_bounds__(192, 1)
             const int H = 1 << g.lh, W = 1 << g.lw;
             long long it = 0;
             bool ok = true;
+            if constexpr (MN) {
+                const int nsa = BM / g.a_cb, nsb = BN / g.b_cb;
+                const int boxw = W < 64 ? W : 64;
+                for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                    const TileCoord tc = tile_coord<true>(g, tile);
+                    for (int kb = 0; kb < tc.nkb; ++kb, ++it) {
+                        const int s = (int)(it % NS);
+                        if (it >= NS && !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((it / NS) - 1) & 1), abort_v)) {
+                            *abort_v = 1;
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t sa = sbase + (uint32_t)(s * Cf::STAGE), sb = sa + Cf::A_BYTES;
+                        const uint32_t bar = smem_u32(&full[s]);
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                                     "r"((uint32_t)Cf::STAGE));
+                        const long long q = tc.kbeg + (long long)kb * BK;      // first pixel of the block
+                        const int b = (int)(q >> (g.lh + g.lw));
+                        const int y = (int)((q >> g.lw) & (H - 1)), x = (int)(q & (W - 1));
+                        (void)boxw;
+                        for (int sg = 0; sg < nsa; ++sg) {
+                            const long long r = tc.m0 + (long long)sg * g.a_cb;
+                            int tap = 4, c = (int)r;
+                            if (g.kind == SUR_OP_TCONV3) {
+                                tap = (int)(r >> g.lc);
+                                c = (int)(r & ((1 << g.lc) - 1));
+                            }
+                            const int dy = ((tap * 11) >> 5) - 1, dx = tap - 3 * (dy + 1) - 1;
+                            // Rows of taps 9.. (M padding) load a box wholly below the tensor: zeros.
+                            const bool tv = tap < 9;
+                            tma_load_4d(sa + (uint32_t)(sg * g.a_cb * 128), &tmA, g.c0 + c, tv ? x + 1 + dx : 0,
+                                        tv ? y + 1 + dy : H + 2, b, bar);
+                        }
+                        for (int sg = 0; sg < nsb; ++sg)
+                            tma_load_4d(sb + (uint32_t)(sg * g.b_cb * 128), &tmB, g.b_c0 + tc.n0 * BN + sg * g.b_cb,
+                                        x + 1, y + 1, b, bar);
+                    }
+                }
+            } else
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 const long long m0 = (long long)(tile / g.ntiles) * BM;
                 const int n0 = (tile % g.ntiles) * BN;
@@ -542,11 +621,12 @@ __global__ void __launch_bounds__(192, 1)
     } else if (warp == 5) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc = make_idesc(BN, false, false);
+            const uint32_t idesc = make_idesc(BN, MN, MN);
             long long it = 0;
             int lt = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+                const int nkb = tile_coord<MN>(g, tile).nkb;
                 const int buf = lt & 1;
                 if (lt >= 2 && !mbar_wait(smem_u32(&tempty[buf]), (uint32_t)(((lt >> 1) - 1) & 1), abort_v)) {
                     *abort_v = 1;
@@ -554,7 +634,7 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t acc_t = tmem + (uint32_t)(buf * BN);
-                for (int kb = 0; kb < g.nkb; ++kb, ++it) {
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = (int)(it % NS);
                     if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((it / NS) & 1), abort_v)) {
                         *abort_v = 1;
@@ -565,6 +645,12 @@ __global__ void __launch_bounds__(192, 1)
                     const uint32_t sa = sbase + (uint32_t)(s * Cf::STAGE), sb = sa + Cf::A_BYTES;
 #pragma unroll
                     for (int k = 0; k < BK / 16; ++k) {
+                        if constexpr (MN) {
+                            const uint64_t da = smem_desc(sa + k * g.a_kstep, g.a_lbo, g.a_sbo, g.a_sw);
+                            const uint64_t db = smem_desc(sb + k * g.b_kstep, g.b_lbo, g.b_sbo, g.b_sw);
+                            mma_bf16(acc_t, da, db, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                            continue;
+                        }
                         uint64_t da;
                         if (ASW == 128) da = smem_desc(sa + k * 32, 16, 1024, 2);
                         else if (ASW == 64) da = smem_desc(sa + (k >> 1) * BOXB + (k & 1) * 32, 16, 512, 4);
@@ -589,9 +675,8 @@ __global__ void __launch_bounds__(192, 1)
                 *abort_v = 1;
                 break;
             }
-            const long long m0 = (long long)(tile / g.ntiles) * BM;
-            const int n0 = (tile % g.ntiles) * BN;
-            epilogue<BN>(g.e, tmem + (uint32_t)(buf * BN), m0, n0, warp, lane);
+            const TileCoord tc = tile_coord<MN>(g, tile);
+            epilogue<BN>(g.e, tmem + (uint32_t)(buf * BN), tc.m0, tc.n0 * BN, warp, lane);
             asm volatile("tcgen05.fence::before_thread_sync;");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])));
         }
@@ -687,12 +772,12 @@ cudaError_t launch_cpasync(const KArgs &g, long long mtiles, int splits, cudaStr
     return cudaGetLastError();
 }
 
-template <int BN, int ASW>
+template <int BN, int ASW, bool MN = false>
 cudaError_t launch_tma(const CUtensorMap &ma, const CUtensorMap &mb, const TArgs &g, long long mtiles,
                        cudaStream_t st)
 {
     static int attr_dev = -1, sms = 0;
-    cudaError_t e = set_smem(k_gemm_tma<BN, ASW>, CfgT<BN>::SMEM, attr_dev);
+    cudaError_t e = set_smem(k_gemm_tma<BN, ASW, MN>, CfgT<BN>::SMEM, attr_dev);
     if (e != cudaSuccess) return e;
     if (!sms) {
         int dev = 0;
@@ -702,9 +787,9 @@ cudaError_t launch_tma(const CUtensorMap &ma, const CUtensorMap &mb, const TArgs
     TArgs gg = g;
     gg.mtiles = (int)mtiles;
     gg.ntiles = g.e.N / BN;
-    const long long tiles = (long long)gg.mtiles * gg.ntiles;
+    const long long tiles = (long long)gg.mtiles * gg.ntiles * (MN ? gg.splits : 1);
     const long long ctas = tiles < 2LL * sms ? tiles : 2LL * sms;   // two resident CTAs per SM
-    k_gemm_tma<BN, ASW><<<(unsigned)ctas, 192, CfgT<BN>::SMEM, st>>>(ma, mb, gg);
+    k_gemm_tma<BN, ASW, MN><<<(unsigned)ctas, 192, CfgT<BN>::SMEM, st>>>(ma, mb, gg);
     return cudaGetLastError();
 }
 
@@ -757,6 +842,75 @@ bool make_maps(const sur_gemm_args &a, int bn, CUtensorMap &ma, CUtensorMap &mb,
     tg.boxw = boxw;
     tg.boxh = boxh;
     tg.b_c0 = a.b.c0;
+    return true;
+}
+
+// Weight-gradient GEMMs: A = TCONV3 or TPIX, B = TPIX on the same pixel grid, dense FP32
+// output.  Rows of A at or beyond `rows` would be read from the tensor (TMA has no row
+// limit inside the channel range), so M must not exceed them.
+bool tma_mn_eligible(const sur_gemm_args &a)
+{
+    if (!g_tma_enabled || a.b.kind != SUR_OP_TPIX) return false;
+    if (a.a.kind != SUR_OP_TCONV3 && a.a.kind != SUR_OP_TPIX) return false;
+    if (a.epi != SUR_EPI_F32_ATOMIC && a.epi != SUR_EPI_F32) return false;
+    if (a.K % 64 || a.a.H != a.b.H || a.a.W != a.b.W || a.a.W < 8 || a.a.H < 1) return false;
+    const long long hw = (long long)a.a.H * a.a.W;
+    if (a.K % hw || a.M > a.a.rows || a.N > a.b.rows) return false;
+    if (hw % 64) return false;
+    if (a.a.kind == SUR_OP_TCONV3 && !(a.a.C == 8 || a.a.C == 32 || a.a.C % 64 == 0)) return false;
+    return true;
+}
+
+// Tensor maps of the MN-major form: (channels, x, y, image) over the halo-padded NHWC
+// tensor, boxes {cb channels, boxw, boxh, 1} of 64 pixels; descriptor fields per cb.
+bool make_maps_mn(const sur_gemm_args &a, int bn, CUtensorMap &ma, CUtensorMap &mb, TArgs &tg)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return false;
+    const int H = a.a.H, W = a.a.W;
+    const long long images = a.K / ((long long)H * W);
+    const int boxw = W < 64 ? W : 64, boxh = 64 / boxw;
+    const int acb = a.a.kind == SUR_OP_TCONV3 ? (a.a.C < 64 ? a.a.C : 64) : 64;
+    const int bcb = bn < 64 ? bn : 64;
+    if (!(acb == 64 || acb == 32 || acb == 8) || !(bcb == 64 || bcb == 32)) return false;
+    auto encode = [&](CUtensorMap &m, const sur_operand &o, int cb) {
+        const size_t e2 = 2;
+        cuuint64_t dims[4] = {(cuuint64_t)o.ld, (cuuint64_t)(W + 2), (cuuint64_t)(H + 2), (cuuint64_t)images};
+        cuuint64_t strides[3] = {o.ld * e2, (cuuint64_t)(W + 2) * o.ld * e2, (cuuint64_t)(H + 2) * (W + 2) * o.ld * e2};
+        cuuint32_t box[4] = {(cuuint32_t)cb, (cuuint32_t)boxw, (cuuint32_t)boxh, 1};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        const CUtensorMapSwizzle sw = cb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                               : (cb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE);
+        return enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(o.p), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!encode(ma, a.a, acb) || !encode(mb, a.b, bcb)) return false;
+    // Descriptor fields: (lbo, sbo, k-step, layout) per channels of the MN atom.
+    auto fields = [](int cb, int &lbo, int &sbo, int &kstep, int &sw) {
+        if (cb == 64) { lbo = 8192; sbo = 1024; kstep = 2048; sw = 2; }
+        else if (cb == 32) { lbo = 4096; sbo = 512; kstep = 1024; sw = 4; }
+        else { lbo = 128; sbo = 1024; kstep = 256; sw = 0; }
+    };
+    fields(acb, tg.a_lbo, tg.a_sbo, tg.a_kstep, tg.a_sw);
+    fields(bcb, tg.b_lbo, tg.b_sbo, tg.b_kstep, tg.b_sw);
+    // A B tile of one MN atom (BN <= 64) never steps between atoms: LBO = SBO makes every
+    // byte the tensor core can address lie inside the tile whichever field it reads.
+    if (bn == bcb) tg.b_lbo = tg.b_sbo;
+    const long long kb = a.K / 64;
+    const long long kbps = (kb + a.splits - 1) / a.splits;
+    tg.kind = a.a.kind;
+    tg.lc = a.a.kind == SUR_OP_TCONV3 ? ilog2(a.a.C) : 0;
+    tg.lh = ilog2(H);
+    tg.lw = ilog2(W);
+    tg.c0 = a.a.c0;
+    tg.b_c0 = a.b.c0;
+    tg.a_cb = acb;
+    tg.b_cb = bcb;
+    tg.K = a.K;
+    tg.kps = kbps * 64;
+    tg.splits = (int)((kb + kbps - 1) / kbps);   // every split non-empty
+    tg.nkb = 0;
     return true;
 }
 
@@ -834,6 +988,17 @@ int gemm(const sur_gemm_args &a, int *status, cudaStream_t st)
     if (mtiles > 0x7FFFFFFF) return SUR_EINVAL;
     const int bn = a.N % 128 == 0 ? 128 : (a.N % 64 == 0 ? 64 : 32);
     cudaError_t err;
+    if (tma_mn_eligible(a)) {
+        CUtensorMap ma, mb;
+        TArgs tg;
+        if (make_maps_mn(a, bn, ma, mb, tg)) {
+            tg.e = e;
+            if (bn == 128) err = launch_tma<128, 16, true>(ma, mb, tg, mtiles, st);
+            else if (bn == 64) err = launch_tma<64, 16, true>(ma, mb, tg, mtiles, st);
+            else err = launch_tma<32, 16, true>(ma, mb, tg, mtiles, st);
+            return err == cudaSuccess ? SUR_OK : SUR_ECUDA;
+        }
+    }
     if (tma_eligible(a)) {
         CUtensorMap ma, mb;
         TArgs tg;

@@ -172,9 +172,13 @@ def test_up_adjoint_gather():
     close(interior(out.cpu().numpy()), ref, absref)
 
 
-@pytest.mark.parametrize("Cin,Cout,splits", [(64, 32, 4), (8, 32, 3), (128, 256, 2)])
-def test_conv_weight_gradient_mn_major_split_k(Cin, Cout, splits):
-    Bn, H, W = 2, 16, 32
+@pytest.mark.parametrize("Cin,Cout,splits,H,W", [(64, 32, 4, 16, 32), (8, 32, 3, 16, 32), (128, 256, 2, 16, 32),
+                                                 (32, 64, 2, 4, 64), (64, 128, 3, 16, 8), (32, 32, 1, 8, 128)])
+def test_conv_weight_gradient_mn_major_split_k(Cin, Cout, splits, H, W):
+    """Weight gradient of a 3x3 convolution (TCONV3 x TPIX, pixels along K, split-K FP32
+    atomics) against the oracle; the shapes cover one- to eight-row pixel boxes and
+    8-, 32- and 64-channel operand atoms."""
+    Bn = 2
     x = bf16_round(gen.normal(size=(Bn, H, W, Cin)))
     X, _ = bf(padded(x))
     dZ, dZd = bf(gen.normal(size=(Bn, H + 2, W + 2, Cout)))
