@@ -200,8 +200,8 @@ int conv_bwd(sur_model *m, int i, int B, const bf16 *X, int ldx, const bf16 *dY,
     const int l = kConvLevel[i];
     const long long M = lvl_pix(m, l, B);
     const int H = lvl_h(m, l), W = lvl_w(m, l);
-    CK(evsur::silu_bwd(dY, ldd, m->Z[i], M, lvl_lh(m, l), lvl_lw(m, l), L.cout, m->dZ, m->stream));
-    CK(evsur::colsum(m->dZ, L.cout, M, lvl_lh(m, l), lvl_lw(m, l), L.cout, m->G + L.b, m->stream));
+    // dZ and, in the same pass, the bias gradient (its column sums).
+    CK(evsur::silu_bwd(dY, ldd, m->Z[i], M, lvl_lh(m, l), lvl_lw(m, l), L.cout, m->dZ, m->G + L.b, m->stream));
     sur_gemm_args g{};
     g.a = gather(SUR_OP_TCONV3, X, ldx, 0, L.cin, 9LL * L.cin, H, W);
     g.b = gather(SUR_OP_TPIX, m->dZ, L.cout, 0, 0, L.cout, H, W);

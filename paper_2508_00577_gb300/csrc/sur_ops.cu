@@ -17,16 +17,45 @@ inline int grid_1d(long long n)
     return (int)(g > 8192 ? 8192 : (g < 1 ? 1 : g));
 }
 
+// Kernels that end in per-channel atomics (block_colsum8): at most 512 blocks, so that
+// each channel's accumulator takes at most 512 atomic additions per call.
+inline int grid_red(long long n)
+{
+    const int g = grid_1d(n);
+    return g > 512 ? 512 : g;
+}
+
 #define GRID_STRIDE(e, total)                                                                    \
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)(total); \
          e += (long long)gridDim.x * blockDim.x)
 
+// Sum over the block of each thread's 8-channel partial sums into out[c] (atomic).  Every
+// thread of a block keeps one channel group, threadIdx.x % C8: the grid stride and the
+// block size (256) are multiples of C8 = C / 8 <= 32.
+__device__ __forceinline__ void block_colsum8(const float acc[8], int C8, float *out)
+{
+    __shared__ float red[256][9];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[threadIdx.x][j] = acc[j];
+    __syncthreads();
+    if ((int)threadIdx.x < C8) {
+        for (int j = 0; j < 8; ++j) {
+            float s = 0.f;
+            for (int k = threadIdx.x; k < 256; k += C8) s += red[k][j];
+            atomicAdd(out + threadIdx.x * 8 + j, s);
+        }
+    }
+}
+
 // dZ = dY * silu'(Z), silu'(z) = s (1 + z (1 - s)) with s = 1 / (1 + e^-z);
 // 8 channels per thread; dZ gets its halo copies (it is gathered by the adjoint
-// convolution).
-__global__ void k_silu_bwd(const bf16 *dY, int ldd, const bf16 *Z, long long M, int lh, int lw, int C, bf16 *dZ)
+// convolution).  dbias (may be NULL) += the column sums of the stored (BF16) dZ over
+// the interior pixels: the bias gradient, without a second pass over dZ.
+__global__ void __launch_bounds__(256) k_silu_bwd(const bf16 *dY, int ldd, const bf16 *Z, long long M, int lh,
+                                                  int lw, int C, bf16 *dZ, float *dbias)
 {
     const int C8 = C >> 3;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     GRID_STRIDE(e, M * C8)
     {
         const long long m = e / C8;
@@ -43,29 +72,33 @@ __global__ void k_silu_bwd(const bf16 *dY, int ldd, const bf16 *Z, long long M, 
             o[j] = __bfloat162float(dh[j]) * s * (1.f + z * (1.f - s));
         }
         const uint4 ov = pack8(o);
+        const bf16 *oh = reinterpret_cast<const bf16 *>(&ov);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += __bfloat162float(oh[j]);
         long long tg[4];
         const int n = halo_targets(m, lh, lw, tg);
         for (int i = 0; i < n; ++i) *reinterpret_cast<uint4 *>(dZ + tg[i] * C + c) = ov;
     }
+    if (dbias) block_colsum8(acc, C8, dbias);
 }
 
-// out[c] += sum over interior pixels of X[pix*ldx + c], c < C (bias gradients).
-// Block (32, 8): threadIdx.x picks the column in a 32-wide slab.
-__global__ void k_colsum(const bf16 *X, int ldx, long long M, int lh, int lw, int C, float *out)
+// out[c] += sum over interior pixels of X[pix*ldx + c], c < C (bias gradients), 8
+// channels (16 bytes) per load.
+__global__ void __launch_bounds__(256) k_colsum(const bf16 *X, int ldx, long long M, int lh, int lw, int C,
+                                                float *out)
 {
-    __shared__ float red[8][33];
-    const int c = blockIdx.x * 32 + threadIdx.x;
-    float acc = 0.f;
-    if (c < C)
-        for (long long m = (long long)blockIdx.y * 8 + threadIdx.y; m < M; m += (long long)gridDim.y * 8)
-            acc += __bfloat162float(X[pad_pix(m, lh, lw) * ldx + c]);
-    red[threadIdx.y][threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.y == 0 && c < C) {
-        float s = 0.f;
-        for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
-        atomicAdd(out + c, s);
+    const int C8 = C >> 3;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    GRID_STRIDE(e, M * C8)
+    {
+        const long long m = e / C8;
+        const int c = (int)(e - m * C8) << 3;
+        const uint4 v = *reinterpret_cast<const uint4 *>(X + pad_pix(m, lh, lw) * ldx + c);
+        const bf16 *h = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += __bfloat162float(h[j]);
     }
+    block_colsum8(acc, C8, out);
 }
 
 // 2x2 average pooling: X (fine grid, ld ldx, first C channels) -> Y (coarse grid
@@ -324,18 +357,17 @@ cudaError_t shift_rho(float *rho, int batch, long long Mb, const float *delta, c
 }
 
 cudaError_t silu_bwd(const bf16 *dY, int ldd, const bf16 *Z, long long M, int lh, int lw, int C, bf16 *dZ,
-                     cudaStream_t st)
+                     float *dbias, cudaStream_t st)
 {
-    k_silu_bwd<<<grid_1d(M * C / 8), 256, 0, st>>>(dY, ldd, Z, M, lh, lw, C, dZ);
+    if (C % 8 || C / 8 > 32) return cudaErrorInvalidValue;
+    k_silu_bwd<<<grid_red(M * C / 8), 256, 0, st>>>(dY, ldd, Z, M, lh, lw, C, dZ, dbias);
     return cudaGetLastError();
 }
 
 cudaError_t colsum(const bf16 *X, int ldx, long long M, int lh, int lw, int C, float *out, cudaStream_t st)
 {
-    long long gy = (M + 8 * 64 - 1) / (8 * 64);
-    if (gy > 1024) gy = 1024;
-    const dim3 grid((C + 31) / 32, (unsigned)(gy < 1 ? 1 : gy)), block(32, 8);
-    k_colsum<<<grid, block, 0, st>>>(X, ldx, M, lh, lw, C, out);
+    if (C % 8 || C / 8 > 32 || ldx % 8 || (reinterpret_cast<uintptr_t>(X) & 15)) return cudaErrorInvalidValue;
+    k_colsum<<<grid_red(M * C / 8), 256, 0, st>>>(X, ldx, M, lh, lw, C, out);
     return cudaGetLastError();
 }
 

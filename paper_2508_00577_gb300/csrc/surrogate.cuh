@@ -74,7 +74,7 @@ int gemm(const sur_gemm_args &a, int *status, cudaStream_t st);
 void set_tma(bool on);
 
 cudaError_t silu_bwd(const bf16 *dY, int ldd, const bf16 *Z, long long M, int lh, int lw, int C, bf16 *dZ,
-                     cudaStream_t st);
+                     float *dbias, cudaStream_t st);
 cudaError_t colsum(const bf16 *X, int ldx, long long M, int lh, int lw, int C, float *out, cudaStream_t st);
 cudaError_t pool2(const bf16 *X, int ldx, long long Mc, int lh, int lw, int C, bf16 *Y, cudaStream_t st);
 cudaError_t unpool2_acc(const bf16 *dY, long long Mc, int lh, int lw, int C, bf16 *dX, int ldx, cudaStream_t st);
