@@ -119,6 +119,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def emit(line, args):
+    """Print the result line and, with --log, append it to a JSON-lines file."""
+    text = json.dumps(line)
+    print(text, flush=True)
+    if getattr(args, "log", None):
+        with open(args.log, "a") as fh:
+            fh.write(text + "\n")
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -191,7 +200,7 @@ def run_reference(args):
                          "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line, args)
     return 0
 
 
@@ -224,6 +233,7 @@ def run(args):
     # Warm-up
     lat.step(args.warmup)
     torch.cuda.synchronize(dev)
+    c_start = lat.conserved()          # FP64 totals (outside the timed region)
 
     # Timed region: one event pair per step on the library's stream.
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -246,8 +256,16 @@ def run(args):
     ms_per_step = total_ms / args.steps
     value = job_mlups(world, N, args.steps, total_ms)
 
-    ok = np.isfinite(lat.conserved()).all()
+    c_end = lat.conserved()
+    ok = np.isfinite(c_end).all()
     lat.close()
+    conservation = {
+        "mass_rel_drift": float(abs(c_end[0] - c_start[0]) / c_start[0]),
+        "momentum_abs_drift": float(np.abs(c_end[1:4] - c_start[1:4]).max()),
+        "energy_population_rel_change": float((c_end[4] - c_start[4]) / c_start[4]),
+        "over_steps": args.steps,
+        "note": "FP64 totals of the FP32 state before and after the timed steps; the energy "
+                "population changes by sum(u.F) per step (Eq. T_shift), mass and momentum are conserved"}
 
     # End to end through the public API with host buffers: init (H2D) + steps + moments (D2H).
     e2e_steps = args.steps
@@ -286,6 +304,7 @@ def run(args):
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "finite": bool(ok),
+        "conservation": conservation,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -308,7 +327,7 @@ def run(args):
         s_line = run_surrogate(sargs)
         line["surrogate"] = {k: s_line[k] for k in ("metric", "value", "unit", "meets_rho_rel_l2_1e-2", "config",
                                                       "plain_lb_seconds", "rollouts", "inference", "training")}
-    print(json.dumps(line), flush=True)
+    emit(line, args)
     return 0
 
 
@@ -633,12 +652,12 @@ def run_surrogate_kernels(args):
         res[name] = (time.perf_counter() - t0) / args.steps * 1e3
     m.close()
     flops = 17.93e9 * bs
-    print(json.dumps({"metric": "surrogate inference TFLOP/s", "value": flops / res["infer"] / 1e9, "unit": "TFLOP/s",
+    emit({"metric": "surrogate inference TFLOP/s", "value": flops / res["infer"] / 1e9, "unit": "TFLOP/s",
                       "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
                       "config": {"workload": f"U-Net on {bs} x {n}^2 domains", "batch": bs},
                       "ms_per_inference": res["infer"], "ms_per_train_step": res["train_step"],
                       "train_tflops": 3 * flops / res["train_step"] / 1e9,
-                      "bf16_peak_tflops": peaks_bf16()}), flush=True)
+                      "bf16_peak_tflops": peaks_bf16()}, args)
     return 0
 
 
@@ -662,6 +681,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement in the default run")
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and 3-D measurements in the default run")
     ap.add_argument("--tile", default="", help="fixed launch shape W,H of the fused kernel")
+    ap.add_argument("--log", default="", help="also append each result line to this JSON-lines file")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate", "surrogate_kernels", "spinodal3d"],
                     help="sweep: the headline droplet Laplace sweep; ensemble: 512 uneven domains; "
                          "surrogate: U-Net surrogate with lattice Boltzmann fallback vs plain LB")
@@ -678,16 +698,16 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         args.domains = args.domains or 512
-        print(json.dumps(run_ensemble(args)), flush=True)
+        emit(run_ensemble(args), args)
         return 0
     if args.workload == "surrogate":
         args.domains = args.domains or 32
-        print(json.dumps(run_surrogate(args)), flush=True)
+        emit(run_surrogate(args), args)
         return 0
     if args.workload == "surrogate_kernels":
         return run_surrogate_kernels(args)
     if args.workload == "spinodal3d":
-        print(json.dumps(run_spinodal3d(args)), flush=True)
+        emit(run_spinodal3d(args), args)
         return 0
     return run(args)
 
