@@ -616,6 +616,35 @@ def run_spinodal3d(args):
             "by_storage": out}
 
 
+def run_coexistence(args):
+    """The paper's Fig. 1 setting on the fused FP32 kernel: isothermal van der Waals slabs
+    (a = 9/392/16, b = 2/21, 8-node interfaces, 8000 steps) over T/Tc = 0.6..0.95; the
+    coexistence densities next to the Maxwell construction of the same EOS."""
+    import oracle.eos as E
+    import paper_2508_00577_gb300 as ev
+    from paper_2508_00577_gb300 import inputs
+
+    a, b = 9 / 392 / 16, 2 / 21
+    _, Tc = E.critical_point(E.VDW, a, b)
+    curve = []
+    for tr in (0.6, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95):
+        RT = tr * Tc
+        rv, rl = E.maxwell(E.VDW, a, b, RT)
+        kappa = E.kappa_for_width(E.VDW, a, b, RT, 8.0)
+        f = inputs.slab(384, 4, rv, rl, RT, thickness=192.0, width=8.0)
+        p = ev.lbm_params.make(nx=384, ny=4, eos=ev.LBM_EOS_VDW, a=a, b=b, kappa=kappa, tau=TAU, thermal=0,
+                               precision=ev.LBM_FP32)
+        with ev.Lattice(p, *f) as g:
+            g.step(8000)
+            rho = g.moments()[0]
+        fin = bool(np.isfinite(rho).all())
+        curve.append({"T_over_Tc": tr, "rho_liquid": float(rho.max()) if fin else None, "rho_vapour":
+                      float(rho.min()) if fin else None, "maxwell_liquid": rl, "maxwell_vapour": rv, "finite": fin})
+    return {"metric": "coexistence curve (Fig. 1 setting)", "unit": "lattice density", "data": "synthetic",
+            "config": {"workload": "isothermal vdW slabs 384 x 4, a = 9/392/16, b = 2/21, width 8, 8000 steps, "
+                                   "fused FP32 D2Q9 kernel"}, "curve": curve}
+
+
 def run_surrogate_kernels(args):
     """Kernel-level timing of the surrogate on batch --batch of 256^2 domains: two
     inferences and one training step (the case the ncu summaries capture), then
@@ -682,7 +711,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and 3-D measurements in the default run")
     ap.add_argument("--tile", default="", help="fixed launch shape W,H of the fused kernel")
     ap.add_argument("--log", default="", help="also append each result line to this JSON-lines file")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate", "surrogate_kernels", "spinodal3d"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate", "surrogate_kernels", "spinodal3d",
+                                                           "coexistence"],
                     help="sweep: the headline droplet Laplace sweep; ensemble: 512 uneven domains; "
                          "surrogate: U-Net surrogate with lattice Boltzmann fallback vs plain LB")
     ap.add_argument("--n3d", type=int, default=256, help="spinodal3d: cube side")
@@ -708,6 +738,9 @@ def main():
         return run_surrogate_kernels(args)
     if args.workload == "spinodal3d":
         emit(run_spinodal3d(args), args)
+        return 0
+    if args.workload == "coexistence":
+        emit(run_coexistence(args), args)
         return 0
     return run(args)
 

@@ -170,6 +170,43 @@ def test_fp32_d3q27(nx, ny, nz, hz, thermal):
         assert rel_rho_err(o, g) <= 1e-5
 
 
+@pytest.mark.parametrize("lam", [0.5, 2.0])
+def test_general_lambda(lam):
+    """lambda != dt (the shifted velocity u* = u + lambda F / rho, the energy shift with
+    lambda^2 and the collision weight (dt/lambda)(1 - beta) of Eq. pre_LBM): FP64
+    populations bit-exact (D2Q9 droplet and a D3Q27 spinodal state), the fused FP32
+    kernels within 1e-5."""
+    fields, kappa = droplet_fields(48, 40, 1, R=12.0)
+    o = oracle.State(oracle.Params(Q=9, nx=48, ny=40, eos=E.CS, a=A, b=B, kappa=kappa, tau=0.3, lambda_=lam),
+                     *fields)
+    o.step(30)
+    for prec in (ev.LBM_FP64, ev.LBM_FP32):
+        p = ev.lbm_params.make(nx=48, ny=40, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=kappa, lambda_=lam, precision=prec)
+        with ev.Lattice(p, *fields) as g:
+            g.step(30)
+            if prec == ev.LBM_FP64:
+                assert_bitexact(o, g)
+            else:
+                assert rel_rho_err(o, g) <= 1e-5
+    _, Tc = E.critical_point(E.CS, A, B)
+    RT = 0.85 * Tc
+    s1, s2 = E.spinodal(E.CS, A, B, RT)
+    k3 = E.kappa_for_width(E.CS, A, B, RT, 4.0)
+    f3 = inputs.spinodal_noise(12, 10, 9, 0.5 * (s1 + s2), RT, amplitude=0.05, D=3)
+    o3 = oracle.State(oracle.Params(Q=27, nx=12, ny=10, nz=9, eos=E.CS, a=A, b=B, kappa=k3, tau=0.3, lambda_=lam),
+                      *f3)
+    o3.step(10)
+    for prec in (ev.LBM_FP64, ev.LBM_FP32):
+        p = ev.lbm_params.make(lattice=ev.LBM_D3Q27, nx=12, ny=10, nz=9, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=k3,
+                               lambda_=lam, precision=prec)
+        with ev.Lattice(p, *f3) as g:
+            g.step(10)
+            if prec == ev.LBM_FP64:
+                assert_bitexact(o3, g)
+            else:
+                assert rel_rho_err(o3, g) <= 1e-5
+
+
 @pytest.mark.parametrize("nx,ny", [(64, 48), (300, 40)])
 def test_fp32_d2q9_isothermal(nx, ny):
     fields, kappa = droplet_fields(nx, ny, 1, tr=0.9)
