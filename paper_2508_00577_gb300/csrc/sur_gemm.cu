@@ -846,8 +846,9 @@ bool make_maps(const sur_gemm_args &a, int bn, CUtensorMap &ma, CUtensorMap &mb,
 }
 
 // Weight-gradient GEMMs: A = TCONV3 or TPIX, B = TPIX on the same pixel grid, dense FP32
-// output.  Rows of A at or beyond `rows` would be read from the tensor (TMA has no row
-// limit inside the channel range), so M must not exceed them.
+// output.  Rows of A at or beyond `rows` must read zero: TCONV3 rows of taps >= 9 load
+// boxes wholly outside the tensor (zeros), so M may exceed `rows` when rows >= 9 C (the
+// K padding of the weights); any other row range must lie inside `rows`.
 bool tma_mn_eligible(const sur_gemm_args &a)
 {
     if (!g_tma_enabled || a.b.kind != SUR_OP_TPIX) return false;
@@ -855,7 +856,8 @@ bool tma_mn_eligible(const sur_gemm_args &a)
     if (a.epi != SUR_EPI_F32_ATOMIC && a.epi != SUR_EPI_F32) return false;
     if (a.K % 64 || a.a.H != a.b.H || a.a.W != a.b.W || a.a.W < 8 || a.a.H < 1) return false;
     const long long hw = (long long)a.a.H * a.a.W;
-    if (a.K % hw || a.M > a.a.rows || a.N > a.b.rows) return false;
+    if (a.K % hw || a.N > a.b.rows) return false;
+    if (a.M > a.a.rows && !(a.a.kind == SUR_OP_TCONV3 && a.a.rows >= 9 * a.a.C)) return false;
     if (hw % 64) return false;
     if (a.a.kind == SUR_OP_TCONV3 && !(a.a.C == 8 || a.a.C == 32 || a.a.C % 64 == 0)) return false;
     return true;
