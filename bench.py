@@ -261,7 +261,7 @@ def run(args):
     lat.close()
     conservation = {
         "mass_rel_drift": float(abs(c_end[0] - c_start[0]) / c_start[0]),
-        "momentum_abs_drift": float(np.abs(c_end[1:4] - c_start[1:4]).max()),
+        "momentum_drift_per_node": float(np.abs(c_end[1:4] - c_start[1:4]).max() / N),
         "energy_population_rel_change": float((c_end[4] - c_start[4]) / c_start[4]),
         "over_steps": args.steps,
         "note": "FP64 totals of the FP32 state before and after the timed steps; the energy "
