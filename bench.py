@@ -35,6 +35,10 @@ BYTES_PER_LU = 2 * 9 * 2 * 4          # D2Q9, f and g, read + write, FP32
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fused2d launch on this workload
 # (profiles/fused2d_d2q9_thermal_fp32.md); None whenever the kernel changes.
 MEASURED_TRAFFIC_BYTES = 1.3353e9
+# DRAM bytes (read + write) of one step of the 512-domain ensemble, from one ncu capture of
+# a one-step launch of k_batch<128> at a 128 x 128 tile (5.949 GB algorithmic;
+# profiles/batch_ensemble_d2q9_fp32.md); None for other tiles or when the kernel changes.
+ENSEMBLE_TRAFFIC_BYTES_PER_STEP = 6.1217e9
 WORKLOAD = "droplet Laplace sweep: 9 x 1024^2 D2Q9 thermal, FP32"
 
 
@@ -312,12 +316,12 @@ def run(args):
         # The other rows, measured on their own workloads: the batched persistent
         # ensemble (A11) and the 3-D path with reduced-precision storage (A10).
         eargs = argparse.Namespace(**vars(args))
-        eargs.domains, eargs.steps, eargs.warmup = 512, 2000, 20
+        eargs.domains, eargs.steps, eargs.warmup, eargs.tile = 512, 2000, 20, ""
         e_line = run_ensemble(eargs)
         line["ensemble"] = {k: e_line[k] for k in ("metric", "value", "unit", "steps", "ms_per_step", "config",
                                                      "roofline", "finite", "finite_domains")}
         sargs3 = argparse.Namespace(**vars(args))
-        sargs3.steps, sargs3.warmup = 20, 3
+        sargs3.steps, sargs3.warmup, sargs3.tile = 20, 3, ""
         line["spinodal3d"] = run_spinodal3d(sargs3)
     if world == 1 and not args.no_surrogate:
         # The learned-surrogate row: speedup of surrogate + fallback over the plain
@@ -353,7 +357,11 @@ def run_ensemble(args):
     params = ev.lbm_params.make(eos=ev.LBM_EOS_CS, a=A, b=B, kappa=KAPPA, tau=TAU, thermal=1, precision=ev.LBM_FP32)
     stream = torch.cuda.Stream()
     bt = ev.Batch(params, sizes, rho, u, T, stream=stream.cuda_stream)
-    tile = bt.autotune(1)
+    if args.tile:                       # fixed W,H launch shape (the one a profile captures)
+        tile = tuple(int(v) for v in args.tile.split(","))
+        bt.set_tile(*tile)
+    else:
+        tile = bt.autotune(1)
     bt.step(args.warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -378,9 +386,12 @@ def run_ensemble(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"ensemble: {len(sizes)} uneven D2Q9 thermal domains (64..512)^2, FP32, "
                                "one persistent launch per call under a CUDA graph",
-                   "nodes": N, "tile": {"w": tile[0], "h": tile[1], "autotuned": True}},
+                   "nodes": N, "tile": {"w": tile[0], "h": tile[1], "autotuned": not args.tile}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "note": f"{BYTES_PER_LU} algorithmic B/LU; peak {peak_kind}"},
+                     "traffic": (ENSEMBLE_TRAFFIC_BYTES_PER_STEP / 1e9
+                                 if len(sizes) == 512 and tuple(tile) == (128, 128) else None),
+                     "traffic_unit": "GB per step (ncu, one-step launch, 128 x 128 tile)",
+                     "note": f"{BYTES_PER_LU} algorithmic B/LU; peak {peak_kind}"},
         "clocks": clk.summary(), "gpu_launches": 1, "finite": n_finite == len(sizes),
         "finite_domains": f"{n_finite}/{len(sizes)}",
     }
