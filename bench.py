@@ -35,6 +35,13 @@ BYTES_PER_LU = 2 * 9 * 2 * 4          # D2Q9, f and g, read + write, FP32
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fused2d launch on this workload
 # (profiles/fused2d_d2q9_thermal_fp32.md); None whenever the kernel changes.
 MEASURED_TRAFFIC_BYTES = 1.3353e9
+# Floating-point operations per lattice update of the FP64 oracle's plain form of the
+# step (every stencil and equilibrium product summed over all Q velocities), counted by
+# running the oracle's source with a counting number type; tests/test_oracle_flops.py
+# checks these values against that count.
+ORACLE_FLOPS_PER_LU = {"d2q9_thermal": 2383, "d3q27_thermal": 10297}
+# FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 operations (FMA) x SM clock.
+FP32_LANES = 152 * 128
 # DRAM bytes (read + write) of one step of the 512-domain ensemble, from one ncu capture of
 # a one-step launch of k_batch<128> at a 128 x 128 tile (5.949 GB algorithmic;
 # profiles/batch_ensemble_d2q9_fp32.md); None for other tiles or when the kernel changes.
@@ -208,6 +215,21 @@ def run_reference(args):
     return 0
 
 
+def alu_check(mlups, flops_per_lu, sm_max_mhz=None):
+    """Where the step would sit against the FP32 ALU roof if the kernel executed the
+    oracle's plain arithmetic: its operation count at the measured update rate, against
+    152 SMs x 128 lanes x 2 x the highest SM clock seen in the timed region (2070 MHz,
+    the GB300's maximum, when no clock was sampled)."""
+    mhz = sm_max_mhz or 2070.0
+    peak = 2 * FP32_LANES * mhz * 1e6 / 1e12
+    tflops = flops_per_lu * mlups * 1e6 / 1e12
+    return {"oracle_flops_per_lu": flops_per_lu, "oracle_equivalent_tflops": tflops,
+            "fp32_peak_tflops": peak, "frac": tflops / peak,
+            "alu_bound_mlups_at_oracle_flops": peak * 1e12 / flops_per_lu / 1e6,
+            "note": "peak derived from unit counts and the sampled max SM clock; the fused kernel "
+                    "folds the arithmetic and executes fewer operations (FMA pipe use in profiles/)"}
+
+
 def run(args):
     import torch
 
@@ -304,6 +326,7 @@ def run(args):
                      "frac": achieved / peak,
                      "traffic": (MEASURED_TRAFFIC_BYTES / 1e9 if nz == 9 else None), "traffic_unit": "GB per launch",
                      "note": f"{BYTES_PER_LU} algorithmic B/LU; peak {peak_kind} copy bandwidth"},
+        "alu_check": alu_check(value, ORACLE_FLOPS_PER_LU["d2q9_thermal"], clk.summary().get("sm_max_mhz")),
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
@@ -582,15 +605,14 @@ def run_spinodal3d(args):
     (algorithmic bytes: 2 populations x 27 x read + write x storage bytes)."""
     import torch
 
-    import oracle.eos as E
     import paper_2508_00577_gb300 as ev
     from paper_2508_00577_gb300 import inputs
 
     n = args.n3d
-    _, Tc = ev.lbm_critical_point(1, A, B)
+    _, Tc = ev.lbm_critical_point(ev.LBM_EOS_CS, A, B)
     RT = 0.85 * Tc
-    s1, s2 = E.spinodal(E.CS, A, B, RT)
-    kappa = E.kappa_for_width(E.CS, A, B, RT, 4.0)
+    s1, s2 = ev.lbm_spinodal(ev.LBM_EOS_CS, A, B, RT)
+    kappa = ev.lbm_kappa_for_width(ev.LBM_EOS_CS, A, B, RT, 4.0)
     rho, u, T = inputs.spinodal_noise(n, n, n, 0.5 * (s1 + s2), RT, amplitude=0.01)
     peak, peak_kind = peaks()
     out = {}
@@ -619,6 +641,8 @@ def run_spinodal3d(args):
                      "tile": tile,
                      "algorithmic_bytes_per_lu": bpl, "achieved_gbs": bpl * p.N / (ms * 1e-3) / 1e9,
                      "frac": bpl * p.N / (ms * 1e-3) / 1e9 / peak, "finite": finite}
+        if prec == ev.LBM_FP32:
+            out[name]["alu_check"] = alu_check(out[name]["mlups"], ORACLE_FLOPS_PER_LU["d3q27_thermal"])
     return {"metric": "MLUPS", "value": out["fp32"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
@@ -631,17 +655,16 @@ def run_coexistence(args):
     """The paper's Fig. 1 setting on the fused FP32 kernel: isothermal van der Waals slabs
     (a = 9/392/16, b = 2/21, 8-node interfaces, 8000 steps) over T/Tc = 0.6..0.95; the
     coexistence densities next to the Maxwell construction of the same EOS."""
-    import oracle.eos as E
     import paper_2508_00577_gb300 as ev
     from paper_2508_00577_gb300 import inputs
 
     a, b = 9 / 392 / 16, 2 / 21
-    _, Tc = E.critical_point(E.VDW, a, b)
+    _, Tc = ev.lbm_critical_point(ev.LBM_EOS_VDW, a, b)
     curve = []
     for tr in (0.6, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95):
         RT = tr * Tc
-        rv, rl = E.maxwell(E.VDW, a, b, RT)
-        kappa = E.kappa_for_width(E.VDW, a, b, RT, 8.0)
+        rv, rl = ev.lbm_coexistence(ev.LBM_EOS_VDW, a, b, RT)
+        kappa = ev.lbm_kappa_for_width(ev.LBM_EOS_VDW, a, b, RT, 8.0)
         f = inputs.slab(384, 4, rv, rl, RT, thickness=192.0, width=8.0)
         p = ev.lbm_params.make(nx=384, ny=4, eos=ev.LBM_EOS_VDW, a=a, b=b, kappa=kappa, tau=TAU, thermal=0,
                                precision=ev.LBM_FP32)

@@ -212,6 +212,22 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  * (no convergence within the iteration limit). */
 int lbm_coexistence(int eos, double a, double b, double RT, double out[2]);
 
+/* Spinodal densities of p = P_E - a rho^2 at RT below the critical value: the two
+ * densities where dp/drho = 0 (the limits of the van der Waals loop of the line of
+ * the paper's Fig. 1), by bisection in FP64 on the host.  out[0] < out[1] (host).
+ * Errors: LBM_EINVAL (NULL out, bad constants, RT <= 0 or RT >= RT_c). */
+int lbm_spinodal(int eos, double a, double b, double RT, double out[2]);
+
+/* Planar liquid-vapour interface of the model's square-gradient free energy (the
+ * capillary term kappa of Eq. EVforce1): kappa/2 (d rho/dx)^2 = omega(rho), omega the
+ * excess grand-potential density between the coexisting densities of lbm_coexistence
+ * (solved on the GPU).  out[0] = 10-90 % width of the density profile, out[1] =
+ * surface tension sigma = int kappa |d rho/dx| d rho (host FP64 quadrature).  The
+ * width scales as sqrt(kappa): kappa for a target width W is kappa (W / width)^2.
+ * Errors: LBM_EINVAL (NULL out, kappa <= 0, or as lbm_coexistence), LBM_ECUDA,
+ * LBM_ETIMEOUT. */
+int lbm_interface(int eos, double a, double b, double RT, double kappa, double out[2]);
+
 /* One FP64 time step that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory while
  * they run -- for example code executing where cudaMalloc is not allowed, or

@@ -26,6 +26,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "evlbm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libevlbm_oracle.so")
+_FC_SRC = os.path.join(_HERE, "flopcount.cpp")
+_FC_PATH = os.path.join(_BUILD, "flopcount")
 _lock = threading.Lock()
 _lib = None
 
@@ -48,11 +50,19 @@ class orc_params(ctypes.Structure):
     ]
 
 
+def _fresh(out, *srcs):
+    return os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build`` (gcc, FP contraction off, OpenMP)."""
+    """Compile the oracle into ``oracle/_build`` (gcc, FP contraction off, OpenMP), and
+    its operation counter (``flopcount.cpp``, g++)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+    if force or not _fresh(_FC_PATH, _FC_SRC, _SRC):
+        tmp = _FC_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-o", tmp, _FC_SRC])
+        os.replace(tmp, _FC_PATH)
+    if not force and _fresh(_LIB_PATH, _SRC):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
@@ -60,6 +70,28 @@ def build(force: bool = False) -> str:
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def flops_per_update(Q=9, thermal=1, eos=1, force_form=0):
+    """Floating-point operations (+, -, *, /) per lattice update of the oracle's step,
+    counted by running the oracle's own source with a counting number type
+    (``flopcount.cpp``).  The step's cost is a N + c (c: a few per-step constants);
+    a is solved from two lattice sizes and checked on a third."""
+    build()
+    runs = []
+    for nx, ny, nz in ((12, 10, 1), (16, 14, 1), (9, 7, 3)):
+        if Q == 9:
+            nz = 1
+        out = subprocess.check_output([_FC_PATH, str(Q), str(thermal), str(eos), str(force_form),
+                                       str(nx), str(ny), str(nz)], text=True).split()
+        one, two, n = (int(v) for v in out)
+        runs.append((n, two - one))
+    (n1, s1), (n2, s2), (n3, s3) = runs
+    a, rem = divmod(s2 - s1, n2 - n1)
+    c = s1 - a * n1
+    if rem or s3 != a * n3 + c:
+        raise RuntimeError(f"operation count is not affine in the node count: {runs}")
+    return a
 
 
 def lib():

@@ -18,7 +18,8 @@ __all__ = [
     "lbm_params", "lib", "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_device",
     "lbm_populations", "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_set_tile",
     "lbm_get_tile", "lbm_autotune", "lbm_sync", "lbm_free",
-    "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "lbm_step_noalloc", "lbm_reset_device",
+    "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "lbm_spinodal", "lbm_interface",
+    "lbm_kappa_for_width", "lbm_step_noalloc", "lbm_reset_device",
     "lbm_save", "lbm_load", "lbm_bounds_violations", "LBMError", "Lattice",
     "LBM_D2Q9", "LBM_D3Q27", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
     "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS", "Batch",
@@ -37,7 +38,7 @@ EXPORTED_SYMBOLS = (
     "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_device", "lbm_populations",
     "lbm_conserved", "lbm_step_count", "lbm_launches_per_step", "lbm_set_tile", "lbm_get_tile",
     "lbm_autotune", "lbm_sync", "lbm_free", "lbm_last_error", "lbm_coexistence", "lbm_critical_point",
-    "lbm_step_noalloc", "lbm_batch_init", "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_tile",
+    "lbm_spinodal", "lbm_interface", "lbm_step_noalloc", "lbm_batch_init", "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_tile",
     "lbm_batch_get_tile", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_batch_nodes",
     "lbm_batch_free", "lbm_batch_last_error", "lbm_reset_device", "lbm_save", "lbm_load",
     "lbm_bounds_violations",
@@ -119,6 +120,9 @@ def lib():
             L.lbm_last_error.restype = ctypes.c_char_p
             L.lbm_coexistence.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.lbm_critical_point.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+            L.lbm_spinodal.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+            L.lbm_interface.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, dp]
             L.lbm_step_noalloc.argtypes = [pp, vp, vp, vp, vp, vp, vp]
             L.lbm_batch_init.argtypes = [pp, ctypes.c_int, ip, ip, dp, dp, dp, vp, ctypes.POINTER(vp)]
             L.lbm_batch_step.argtypes = [vp, ctypes.c_int]
@@ -277,6 +281,29 @@ def lbm_critical_point(eos, a, b):
     if rc != LBM_OK:
         raise LBMError(rc, "lbm_critical_point")
     return float(out[0]), float(out[1])
+
+
+def lbm_spinodal(eos, a, b, RT):
+    out = np.zeros(2)
+    rc = lib().lbm_spinodal(int(eos), float(a), float(b), float(RT), _dptr(out))
+    if rc != LBM_OK:
+        raise LBMError(rc, "lbm_spinodal")
+    return float(out[0]), float(out[1])
+
+
+def lbm_interface(eos, a, b, RT, kappa):
+    """(10-90 % width, surface tension) of the planar interface at RT with capillarity kappa."""
+    out = np.zeros(2)
+    rc = lib().lbm_interface(int(eos), float(a), float(b), float(RT), float(kappa), _dptr(out))
+    if rc != LBM_OK:
+        raise LBMError(rc, "lbm_interface")
+    return float(out[0]), float(out[1])
+
+
+def lbm_kappa_for_width(eos, a, b, RT, width):
+    """kappa whose planar interface has the 10-90 % width `width` (width ~ sqrt(kappa))."""
+    w1, _ = lbm_interface(eos, a, b, RT, 1.0)
+    return (float(width) / w1) ** 2
 
 
 def lbm_step_noalloc(params: lbm_params, d_f, d_g, d_RT, d_f_out, d_g_out, stream=0):

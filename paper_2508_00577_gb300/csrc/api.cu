@@ -566,6 +566,24 @@ int lbm_coexistence(int eos, double a, double b, double RT, double out[2])
     return LBM_OK;
 }
 
+int lbm_spinodal(int eos, double a, double b, double RT, double out[2])
+{
+    double crit[2];
+    if (!out || lbm_critical_point(eos, a, b, crit) != LBM_OK) return LBM_EINVAL;
+    if (!(RT > 0.0) || !(RT < crit[1])) return LBM_EINVAL;
+    return evlbm::spinodal(eos, a, b, RT, crit[0], out) ? LBM_EINVAL : LBM_OK;
+}
+
+int lbm_interface(int eos, double a, double b, double RT, double kappa, double out[2])
+{
+    if (!out || !(kappa > 0.0)) return LBM_EINVAL;
+    double co[2];
+    const int rc = lbm_coexistence(eos, a, b, RT, co);
+    if (rc != LBM_OK) return rc;
+    evlbm::interface(eos, a, b, RT, kappa, co[0], co[1], &out[0], &out[1]);
+    return LBM_OK;
+}
+
 
 // ---------------------------------------------------------------------------
 // Checkpoint and resume.  File layout (little-endian, fixed-width fields):

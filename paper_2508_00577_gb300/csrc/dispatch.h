@@ -62,6 +62,11 @@ cudaError_t totals(int prec, int Q, const KParams &p, const void *f, const void 
 
 // Maxwell construction in FP64 on the GPU.
 cudaError_t coexistence(int eos, double a, double b, double RT, double rho_c, double *h_out, int *h_status);
+// Spinodal densities (host); returns 1 above the critical temperature.
+int spinodal(int eos, double a, double b, double RT, double rho_c, double out[2]);
+// 10-90 % width and tension of the planar square-gradient interface (host).
+void interface(int eos, double a, double b, double RT, double kappa, double rv, double rl, double *width,
+               double *sigma);
 
 // Out-of-range accesses counted by the fused kernels of a bounds-checked build
 // (-DEVLBM_BOUNDS_CHECK): the count, -1 when the library was built without the

@@ -104,21 +104,21 @@ cudaError_t totals_s(int Q, const KParams &p, const void *f, const void *g, cons
 struct Eos {
     int kind;
     double a, b, RT;
-    __device__ double rho_max() const { return kind == 0 ? 1.0 / b : 4.0 / b; }
-    __device__ double p(double r) const
+    __host__ __device__ double rho_max() const { return kind == 0 ? 1.0 / b : 4.0 / b; }
+    __host__ __device__ double p(double r) const
     {
         if (kind == 0) return r * RT / (1.0 - b * r) - a * r * r;
         const double e = 0.25 * b * r;
         return r * RT * (1.0 + e + e * e - e * e * e) / ((1.0 - e) * (1.0 - e) * (1.0 - e)) - a * r * r;
     }
-    __device__ double dp(double r) const
+    __host__ __device__ double dp(double r) const
     {
         if (kind == 0) return RT / ((1.0 - b * r) * (1.0 - b * r)) - 2.0 * a * r;
         const double e = 0.25 * b * r, om = 1.0 - e;
         return RT * (1.0 + 4.0 * e + 4.0 * e * e - 4.0 * e * e * e + e * e * e * e) / (om * om * om * om) -
                2.0 * a * r;
     }
-    __device__ double mu(double r) const
+    __host__ __device__ double mu(double r) const
     {
         if (kind == 0) return RT * (log(r / (1.0 - b * r)) + b * r / (1.0 - b * r)) - 2.0 * a * r;
         const double e = 0.25 * b * r, om = 1.0 - e;
@@ -128,7 +128,7 @@ struct Eos {
 
 // Root of a monotone function on [lo, hi] by bisection (fixed number of halvings).
 template <typename Fn>
-__device__ double bisect(Fn fn, double lo, double hi, int halvings)
+__host__ __device__ double bisect(Fn fn, double lo, double hi, int halvings)
 {
     double flo = fn(lo);
     for (int k = 0; k < halvings; ++k) {
@@ -186,6 +186,41 @@ __global__ void k_coexistence(Eos E, double rho_c, double *out, int *status)
 }
 
 }  // namespace
+
+int spinodal(int eos, double a, double b, double RT, double rho_c, double out[2])
+{
+    const Eos E{eos, a, b, RT};
+    const double rmax = E.rho_max() * (1.0 - 1e-12);
+    out[0] = bisect([&](double r) { return E.dp(r); }, 1e-12 * rho_c, rho_c, 200);
+    out[1] = bisect([&](double r) { return E.dp(r); }, rho_c, rmax, 200);
+    return E.dp(0.5 * (out[0] + out[1])) < 0.0 ? 0 : 1;
+}
+
+// Planar interface of square-gradient theory between the coexisting densities:
+// kappa/2 (d rho/dx)^2 = omega(rho), omega(rho) = int_{rho_v}^{rho} (mu(s) - mu_sat) ds
+// (the excess grand-potential density; it vanishes at both coexisting densities because
+// their pressures and chemical potentials are equal).  omega is accumulated on a uniform
+// grid of 10 M cells by Simpson's rule in each cell; the 10-90 % width integrates
+// |d rho/dx|^-1 over the cells M .. 9M (rho_v + 0.1 .. 0.9 (rho_l - rho_v)) and the
+// tension sigma = int kappa |d rho/dx| d rho over all cells, both by the trapezoid rule.
+void interface(int eos, double a, double b, double RT, double kappa, double rv, double rl, double *width,
+               double *sigma)
+{
+    const Eos E{eos, a, b, RT};
+    const int M = 8192, cells = 10 * M;
+    const double h = (rl - rv) / cells, mu_sat = E.mu(rv);
+    double omega = 0.0, w = 0.0, sg = 0.0, grad0 = 0.0;
+    for (int k = 0; k < cells; ++k) {
+        const double r0 = rv + k * h, r1 = rv + (k + 1) * h;
+        omega += h / 6.0 * ((E.mu(r0) - mu_sat) + 4.0 * (E.mu(0.5 * (r0 + r1)) - mu_sat) + (E.mu(r1) - mu_sat));
+        const double grad1 = sqrt(fmax(2.0 * omega / kappa, 0.0));     // |d rho/dx| at r1
+        sg += 0.5 * h * kappa * (grad0 + grad1);
+        if (k >= M && k < 9 * M) w += 0.5 * h * (1.0 / grad0 + 1.0 / grad1);
+        grad0 = grad1;
+    }
+    *width = w;
+    *sigma = sg;
+}
 
 size_t totals_work_bytes(long long) { return sizeof(double) * (5 * kRedBlocks + 8) + 64; }
 
