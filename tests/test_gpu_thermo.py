@@ -21,12 +21,15 @@ def test_spinodal_interface_and_kappa_match_oracle(eos, a, b, tr):
     s = ev.lbm_spinodal(eos, a, b, RT)
     so = E.spinodal(eos, a, b, RT)
     assert s[0] == pytest.approx(so[0], rel=1e-12) and s[1] == pytest.approx(so[1], rel=1e-12)
+    # The oracle's 10-90 % band is the set of its 2e5 grid points inside it, so its width
+    # can miss up to one cell at each end: 2 / (0.8 * 2e5) = 1.25e-5 relative (the
+    # library's grid has nodes on both band edges).  kappa ~ width^-2 doubles that.
     w, sigma = ev.lbm_interface(eos, a, b, RT, 0.5)
     wo, sigmao = E.interface(eos, a, b, RT, 0.5)
-    assert w == pytest.approx(wo, rel=1e-6)
+    assert w == pytest.approx(wo, rel=2e-5)
     assert sigma == pytest.approx(sigmao, rel=1e-6)
     assert ev.lbm_kappa_for_width(eos, a, b, RT, 4.0) == pytest.approx(E.kappa_for_width(eos, a, b, RT, 4.0),
-                                                                       rel=2e-6)
+                                                                       rel=4e-5)
 
 
 def test_thermo_helpers_reject_bad_input():
