@@ -50,6 +50,11 @@ extern "C" {
 #define LBM_D2Q9 0
 #define LBM_D3Q27 1
 
+/* tile_h of lbm_set_tile (D2Q9 FP32) selecting the balanced persistent grid: per
+ * strip, as many CTAs as fit on the GPU at once divided by the strip count, each
+ * taking an equal share of that strip's row pairs over all layers. */
+#define LBM_TILE_BALANCED (-1)
+
 #define LBM_EOS_VDW 0        /* P_E = rho RT / (1 - b rho)  (the paper's form) */
 #define LBM_EOS_CS 1         /* Carnahan-Starling contact value, eta = b rho / 4 */
 
@@ -177,7 +182,10 @@ int lbm_launches_per_step(const lbm_ctx *ctx);
 
 /* Launch shape of the fused single-pass kernel (used for D2Q9 at FP32): strips of
  * tile_w columns (one of 64, 96, 128, 192) marching over chunks of tile_h rows
- * (>= 1; rounded up to an even number, the kernel advances two rows at a time).
+ * (>= 1; rounded up to an even number, the kernel advances two rows at a time), or
+ * tile_h = LBM_TILE_BALANCED: a grid of about one CTA per resident slot of the GPU
+ * (SMs x CTAs per SM, rounded down to a multiple of the strip count), each taking an
+ * equal share of one strip's row pairs.  lbm_autotune times both kinds.
  * tile_w = tile_h = 0 restores the size-based default.  Contexts without a fused
  * kernel accept and ignore the shape.  Errors: LBM_EINVAL. */
 int lbm_set_tile(lbm_ctx *ctx, int tile_w, int tile_h);

@@ -21,12 +21,13 @@ __all__ = [
     "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "lbm_spinodal", "lbm_interface",
     "lbm_kappa_for_width", "lbm_step_noalloc", "lbm_reset_device",
     "lbm_save", "lbm_load", "lbm_bounds_violations", "LBMError", "Lattice",
-    "LBM_D2Q9", "LBM_D3Q27", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
+    "LBM_D2Q9", "LBM_D3Q27", "LBM_TILE_BALANCED", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
     "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS", "Batch",
 ]
 
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENOMEM, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EIO = 0, -1, -2, -3, -4, -5, -6
 LBM_D2Q9, LBM_D3Q27 = 0, 1
+LBM_TILE_BALANCED = -1
 LBM_EOS_VDW, LBM_EOS_CS = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
 

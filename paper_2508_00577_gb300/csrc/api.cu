@@ -400,8 +400,10 @@ int lbm_set_tile(lbm_ctx *c, int tile_w, int tile_h)
         if (!ok) return fail(c, LBM_EINVAL, "D3Q27: tile_w must be 16 and tile_h (z-chunk) >= 1 (or both 0)");
     } else {
         for (int k = 0; k < evlbm::kFusedWidthCount; ++k)
-            ok = ok || (tile_w == evlbm::kFusedWidths[k] && tile_h >= 1);
-        if (!ok) return fail(c, LBM_EINVAL, "tile_w must be one of 64,96,128,192 and tile_h >= 1 (or both 0)");
+            ok = ok || (tile_w == evlbm::kFusedWidths[k] && (tile_h >= 1 || tile_h == LBM_TILE_BALANCED));
+        if (!ok)
+            return fail(c, LBM_EINVAL,
+                        "tile_w must be one of 64,96,128,192 and tile_h >= 1 or LBM_TILE_BALANCED (or both 0)");
     }
     c->K.tile_w = tile_w;
     c->K.tile_h = tile_h;
@@ -468,7 +470,7 @@ int lbm_autotune(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
     cudaEvent_t e0, e1;
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
-    const int heights[] = {16, 32, 64, 128, 256};
+    const int heights[] = {16, 32, 64, 128, 256, LBM_TILE_BALANCED};
     const int nx = c->cur ^ 1;
     float best = 1e30f;
     int bw = 0, bh = 0;
@@ -477,9 +479,9 @@ int lbm_autotune(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
     for (int wi = 0; wi < evlbm::kFusedWidthCount && e == cudaSuccess; ++wi) {
         const int W = evlbm::kFusedWidths[wi];
         if (W > 2 * c->P.nx && W != evlbm::kFusedWidths[0]) continue;
-        for (int hi = 0; hi < 5 && e == cudaSuccess; ++hi) {
-            const int H = heights[hi] < c->P.ny ? heights[hi] : c->P.ny;
-            if (hi > 0 && H == (heights[hi - 1] < c->P.ny ? heights[hi - 1] : c->P.ny)) continue;
+        for (int hi = 0; hi < 6 && e == cudaSuccess; ++hi) {
+            const int H = heights[hi] < c->P.ny ? heights[hi] : c->P.ny;    // the balanced grid stays -1
+            if (hi > 0 && hi < 5 && H == (heights[hi - 1] < c->P.ny ? heights[hi - 1] : c->P.ny)) continue;
             K.tile_w = W;
             K.tile_h = H;
             // One untimed launch, then probe_steps timed ones; input stays c->f[c->cur].

@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_batch(Bat
         A.lambda = B.lambda;
         A.c_eq = B.c_eq;
         A.c_star = B.c_star;
-        fused_tile<kW, THERMAL, true>(A, k % D.strips, k / D.strips, 0, smem);
+        const int y0 = (k / D.strips) * D.H;
+        fused_tile<kW, THERMAL, true>(A, k % D.strips, y0, min(D.H, D.ny - y0), 0, smem);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();

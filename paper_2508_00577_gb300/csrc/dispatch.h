@@ -42,6 +42,8 @@ struct FieldOffsets {
 // launch shape is a strip of tile_w columns marching over chunks of tile_h rows
 // (KParams::tile_w/tile_h; 0 = default).
 constexpr int kFusedWidthCount = 4;
+// tile_h of the D2Q9 kernel that selects the balanced persistent grid (LBM_TILE_BALANCED).
+constexpr int kTileBalanced = -1;
 extern const int kFusedWidths[kFusedWidthCount];
 void fused2d_default_tile(const KParams &p, int *W, int *H);
 bool fused2d_supported(int prec, int Q, const KParams &p);

@@ -126,11 +126,12 @@ __device__ __forceinline__ v2 sum9(const v2 h[9])
     return ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
 }
 
-// One strip x chunk tile of one layer: strip bx, chunk by, layer bz.  smem holds
-// smem_of<kW>() bytes.  CG selects loads through L2 only (needed when the
-// populations were written by other CTAs of the same launch).
+// One tile: rows y0 .. y0 + rows - 1 (y0 even, y0 + rows <= ny) of strip bx of layer
+// bz.  smem holds smem_of<kW>() bytes.  CG selects loads that may see populations
+// written by other CTAs of the same launch.  A CTA that runs several tiles must pass a
+// barrier between them (the rings are reused).
 template <int kW, bool THERMAL, bool CG>
-__device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, int bz, v2 *smem)
+__device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, int rows, int bz, v2 *smem)
 {
     constexpr int S = slots_of<kW>();
     enum { RHO, JX, JY, PXX, PXY, PYY, UX, UY, QX, QY, WQ };
@@ -143,8 +144,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int by, i
     const int t = threadIdx.x;
     const int x0 = bx * kW;
     const int Weff = min(kW, nx - x0);
-    const int y0 = by * A.H;                              // H is even
-    const int Heff = min(A.H, ny - y0);
+    const int Heff = rows;
     const unsigned layer = (unsigned)bz * (unsigned)nx * (unsigned)ny;
 
     // Column role.

@@ -34,7 +34,7 @@ def check(name, o, rho):
 
 for (nx, ny, nz) in [(7, 5, 1), (130, 70, 2), (257, 33, 1), (1, 1, 1)]:
     for W in (64, 96, 128, 192):
-        for H in (2, 6, 64):
+        for H in (2, 6, 64, ev.LBM_TILE_BALANCED):
             f = inputs.spinodal_noise(nx, ny, nz, 0.5 * (s1 + s2), RT, amplitude=0.05, D=2)
             p = ev.lbm_params.make(nx=nx, ny=ny, nz=nz, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=kappa, precision=ev.LBM_FP32)
             with ev.Lattice(p, *f) as g:
@@ -84,7 +84,7 @@ def test_checked_library_meets_no_out_of_range_index():
     assert r.returncode == 0, r.stderr[-3000:]
     res = json.loads(r.stdout.split("RESULT ", 1)[1])
     assert res["start"] == 0
-    assert len(res["cases"]) == 4 * 4 * 3 + 4 + 3
+    assert len(res["cases"]) == 4 * 4 * 4 + 4 + 3
     for name, err, oob in res["cases"]:
         assert oob == 0, f"{name}: {oob} out-of-range indices"
         assert err <= 1e-5, f"{name}: max rel rho error {err}"

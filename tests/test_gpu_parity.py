@@ -324,8 +324,9 @@ def test_conserved_flags_nonfinite():
 
 
 def test_fp32_every_launch_shape():
-    """Every strip width and several row-chunk heights (down to one row) give the
-    same FP32 result within 1e-5 of the oracle (ragged strips and chunks included)."""
+    """Every strip width and several row-chunk heights (down to one row), and the
+    balanced persistent grid, give the same FP32 result within 1e-5 of the oracle
+    (ragged strips and chunks included)."""
     nx, ny = 300, 70
     fields, kappa = droplet_fields(nx, ny, 1)
     o, _ = pair(9, nx, ny, 1, fields, kappa, ev.LBM_FP32)
@@ -333,7 +334,7 @@ def test_fp32_every_launch_shape():
     ro = o.macro()[0]
     gp = ev.lbm_params.make(nx=nx, ny=ny, kappa=kappa, precision=ev.LBM_FP32)
     for W in (64, 96, 128, 192):
-        for H in (1, 5, 64, 70):
+        for H in (1, 5, 64, 70, ev.LBM_TILE_BALANCED):
             with ev.Lattice(gp, *fields) as g:
                 ev.lbm_set_tile(g.ctx, W, H)
                 g.step(30)
@@ -348,9 +349,11 @@ def test_autotune_keeps_state():
         g.step(5)
         f0, g0 = g.populations()
         w, h = ev.lbm_autotune(g.ctx, 2)
-        assert w in (64, 96, 128, 192) and 1 <= h <= 150
+        assert w in (64, 96, 128, 192) and (1 <= h <= 150 or h == ev.LBM_TILE_BALANCED)
         assert ev.lbm_get_tile(g.ctx) == (w, h)
         f1, g1 = g.populations()
         assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
         with pytest.raises(ev.LBMError):
             ev.lbm_set_tile(g.ctx, 100, 10)
+        with pytest.raises(ev.LBMError):
+            ev.lbm_set_tile(g.ctx, 128, -2)
