@@ -32,9 +32,11 @@ TRS = (0.7, 0.8, 0.9)
 RADII = (64.0, 128.0, 256.0)
 A, B, KAPPA, TAU = 0.1, 4.0, 0.116, 0.3
 BYTES_PER_LU = 2 * 9 * 2 * 4          # D2Q9, f and g, read + write, FP32
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_fused2d launch on this workload
-# (profiles/fused2d_d2q9_thermal_fp32.md); None whenever the kernel changes.
-MEASURED_TRAFFIC_BYTES = 1.3353e9
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch on this workload, per launch
+# shape (W, H) of the fused kernel (H = -1: the balanced grid, k_fused2d_bal), from one ncu
+# capture each (profiles/fused2d_d2q9_thermal_fp32.md); a shape without a capture, or a
+# changed kernel, reports None.
+MEASURED_TRAFFIC_BYTES = {(128, 256): 1.3353e9}
 # Floating-point operations per lattice update of the FP64 oracle's plain form of the
 # step (every stencil and equilibrium product summed over all Q velocities), counted by
 # running the oracle's source with a counting number type; tests/test_oracle_flops.py
@@ -324,7 +326,9 @@ def run(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (MEASURED_TRAFFIC_BYTES / 1e9 if nz == 9 else None), "traffic_unit": "GB per launch",
+                     "traffic": (MEASURED_TRAFFIC_BYTES[tuple(tile)] / 1e9
+                                 if nz == 9 and tuple(tile) in MEASURED_TRAFFIC_BYTES else None),
+                     "traffic_unit": "GB per launch",
                      "note": f"{BYTES_PER_LU} algorithmic B/LU; peak {peak_kind} copy bandwidth"},
         "alu_check": alu_check(value, ORACLE_FLOPS_PER_LU["d2q9_thermal"], clk.summary().get("sm_max_mhz")),
         "clocks": clk.summary(),
