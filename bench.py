@@ -520,7 +520,7 @@ def run_surrogate(args):
     t_train = time.perf_counter() - t0
     del snaps, view, x, y, vx, vy
 
-    # Held-out domains: the plain lattice Boltzmann run is the reference and the judge.
+    # Held-out domains: the plain lattice Boltzmann run is the reference every error is measured against.
     nd = len(test_doms)
     N = nd * Mb
     rho0, u0, T0 = surrogate_fields(ev, test_doms, Tc)

@@ -5,7 +5,8 @@
  * later (it predicts the increment).  The lattice Boltzmann method of the paper
  * (Sec. 3, Eqs. for the moments, the shifted equilibria and the relaxation,
  * implemented in evlbm.h) generates its training data, is its fallback and
- * judges its error; the paper itself has no learned component, so nothing in
+ * is the reference its error is measured against; the paper itself has no learned
+ * component, so nothing in
  * this header restates a passage of it beyond that.
  *
  * Arithmetic: BF16 weights and activations, FP32 accumulation on the tensor
