@@ -6,8 +6,7 @@
  * (Sec. 3, Eqs. for the moments, the shifted equilibria and the relaxation,
  * implemented in evlbm.h) generates its training data, is its fallback and
  * is the reference its error is measured against; the paper itself has no learned
- * component, so nothing in
- * this header restates a passage of it beyond that.
+ * component, so nothing in this header restates a passage of it beyond that.
  *
  * Arithmetic: BF16 weights and activations, FP32 accumulation on the tensor
  * cores (tcgen05.mma kind::f16), FP32 master weights, gradients and Adam
