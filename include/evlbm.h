@@ -287,7 +287,9 @@ int lbm_batch_step(lbm_batch *b, int n_steps);
  * (host FP64; any may be NULL).  Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */
 int lbm_batch_moments(lbm_batch *b, int domain, double *rho, double *u, double *T);
 
-/* Launch shape of the tiles (as lbm_set_tile; tile_w in 64, 96, 128, 192). */
+/* Launch shape of the work items (as lbm_set_tile: tile_w in 64, 96, 128, 192,
+ * tile_h >= 1; LBM_TILE_BALANCED does not apply, the persistent launch already takes
+ * items as CTAs free up).  Errors: LBM_EINVAL. */
 int lbm_batch_set_tile(lbm_batch *b, int tile_w, int tile_h);
 int lbm_batch_get_tile(const lbm_batch *b, int *tile_w, int *tile_h);
 
