@@ -60,8 +60,13 @@ extern "C" {
 
 #define LBM_FP64 0           /* FP64 storage and arithmetic (bit-exact reference order) */
 #define LBM_FP32 1           /* FP32 storage and arithmetic */
-#define LBM_FP16_DEV 2       /* FP16 storage of f_i - w_i rho_ref, g_i - w_i rho_ref E_ref; FP32 arithmetic */
-#define LBM_BF16_DEV 3       /* BF16 storage of the same deviations; FP32 arithmetic */
+/* 16-bit storage: each population is stored as its deviation from the local
+ * equilibrium of the node that wrote it, scaled by its weight,
+ *   (h_i - h_i^eq(R)) / (w_i rho_R)   (g: / (w_i rho_R 3/2 RT_R)),
+ * with that node's reference state R = (rho, u, theta0, RT) stored beside the
+ * populations in the same format; arithmetic is FP32. */
+#define LBM_FP16_DEV 2       /* FP16 deviation storage */
+#define LBM_BF16_DEV 3       /* BF16 deviation storage */
 
 typedef struct lbm_ctx lbm_ctx;
 
@@ -180,7 +185,9 @@ int lbm_load(lbm_ctx *ctx, const char *path);
  * -1 for NULL. */
 int lbm_launches_per_step(const lbm_ctx *ctx);
 
-/* Launch shape of the fused single-pass kernel (used for D2Q9 at FP32): strips of
+/* Launch shape of the fused single-pass kernels (used at FP32).  D3Q27: tile_w = 16
+ * (16 x 16 columns per CTA) and tile_h = the z-chunk a CTA marches through (>= 1).
+ * D2Q9: strips of
  * tile_w columns (one of 64, 96, 128, 192) marching over chunks of tile_h rows
  * (>= 1; rounded up to an even number, the kernel advances two rows at a time), or
  * tile_h = LBM_TILE_BALANCED: a grid of about one CTA per resident slot of the GPU
