@@ -45,17 +45,20 @@ def test_sweep_full_size_in_bench_launch_shape():
     with ev.Lattice(p, rho, u, T) as g:
         tile = ev.lbm_autotune(g.ctx, 1)
     steps = 10
-    with ev.Lattice(p, rho, u, T) as g:
-        ev.lbm_set_tile(g.ctx, *tile)
-        g.step(steps)
-        gr, gu, gT, _ = g.moments()
     o = oracle.State(oracle.Params(Q=9, nx=n, ny=n, nz=nz, eos=E.CS, a=bench.A, b=bench.B, kappa=bench.KAPPA,
                                    tau=bench.TAU), rho, u, T)
     o.step(steps)
     orho, ou, oT = o.macro()[:3]
-    er, eT, eu = compare(orho, ou, oT, gr, gu, gT, 1e-5)
-    print(f"\nsweep 9 x 1024^2, tile {tile}: max rel rho {er:.2e}, T {eT:.2e}, max abs u {eu:.2e}")
-    assert er <= 1e-5 and eT <= 1e-5 and eu <= 1e-6
+    # The autotuned shape, and both shapes the autotuner chooses between on this workload
+    # (128-column strips in 256-row chunks, or the balanced persistent grid).
+    for shape in dict.fromkeys([tuple(tile), (128, 256), (128, ev.LBM_TILE_BALANCED)]):
+        with ev.Lattice(p, rho, u, T) as g:
+            ev.lbm_set_tile(g.ctx, *shape)
+            g.step(steps)
+            gr, gu, gT, _ = g.moments()
+        er, eT, eu = compare(orho, ou, oT, gr, gu, gT, 1e-5)
+        print(f"\nsweep 9 x 1024^2, tile {shape}: max rel rho {er:.2e}, T {eT:.2e}, max abs u {eu:.2e}")
+        assert er <= 1e-5 and eT <= 1e-5 and eu <= 1e-6, shape
 
 
 def test_ensemble_full_size_sampled_domains():
