@@ -121,6 +121,27 @@ def test_critical_point_host(eos, a, b):
     assert Tc == pytest.approx(oTc, rel=1e-10)
 
 
+@pytest.mark.parametrize("eos,a,b", [(ev.LBM_EOS_CS, 0.1, 4.0), (ev.LBM_EOS_VDW, 9 / 392, 2 / 21)])
+def test_spinodal_host(eos, a, b):
+    """lbm_spinodal is a host computation: checked against the oracle without a GPU."""
+    _, Tc = E.critical_point(eos, a, b)
+    for tr in (0.6, 0.8, 0.95):
+        s1, s2 = ev.lbm_spinodal(eos, a, b, tr * Tc)
+        o1, o2 = E.spinodal(eos, a, b, tr * Tc)
+        assert s1 == pytest.approx(o1, rel=1e-12) and s2 == pytest.approx(o2, rel=1e-12)
+
+
+def test_thermo_helpers_reject_invalid_arguments_on_host():
+    _, Tc = ev.lbm_critical_point(ev.LBM_EOS_CS, 0.1, 4.0)
+    L = ev.lib()
+    out = np.zeros(2)
+    ptr = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert L.lbm_spinodal(ev.LBM_EOS_CS, 0.1, 4.0, 1.01 * Tc, ptr) == ev.LBM_EINVAL
+    assert L.lbm_spinodal(ev.LBM_EOS_CS, 0.1, 4.0, 0.8 * Tc, None) == ev.LBM_EINVAL
+    assert L.lbm_interface(ev.LBM_EOS_CS, 0.1, 4.0, 0.8 * Tc, 0.0, ptr) == ev.LBM_EINVAL
+    assert L.lbm_interface(ev.LBM_EOS_CS, 0.1, 4.0, 1.2 * Tc, 1.0, ptr) == ev.LBM_EINVAL
+
+
 def test_coexistence_rejects_supercritical_on_host():
     _, Tc = ev.lbm_critical_point(ev.LBM_EOS_CS, 0.1, 4.0)
     with pytest.raises(ev.LBMError) as e:

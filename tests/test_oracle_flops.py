@@ -29,3 +29,13 @@ def test_counts_are_per_node_and_ordered():
 def test_bench_reports_the_counted_values():
     assert bench.ORACLE_FLOPS_PER_LU["d2q9_thermal"] == oracle.flops_per_update(9, 1, 1, 0)
     assert bench.ORACLE_FLOPS_PER_LU["d3q27_thermal"] == oracle.flops_per_update(27, 1, 1, 0)
+
+
+def test_alu_check_arithmetic():
+    """bench.alu_check: peak = 2 x 152 x 128 lanes x clock; operations per second =
+    operations per update x updates per second."""
+    r = bench.alu_check(1000.0, 2000, 2000.0)          # 1 GLUPS, 2000 ops per update, 2 GHz
+    assert r["fp32_peak_tflops"] == 2 * 152 * 128 * 2.0e9 / 1e12
+    assert abs(r["oracle_equivalent_tflops"] - 2.0) < 1e-12
+    assert abs(r["frac"] - 2.0 / r["fp32_peak_tflops"]) < 1e-12
+    assert abs(r["alu_bound_mlups_at_oracle_flops"] - r["fp32_peak_tflops"] * 1e12 / 2000 / 1e6) < 1e-6
