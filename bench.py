@@ -44,10 +44,10 @@ MEASURED_TRAFFIC_BYTES = {(128, 256): 1.3353e9, (128, -1): 1.3384e9}
 ORACLE_FLOPS_PER_LU = {"d2q9_thermal": 2383, "d3q27_thermal": 10297}
 # FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 operations (FMA) x SM clock.
 FP32_LANES = 152 * 128
-# DRAM bytes (read + write) of one step of the 512-domain ensemble, from one ncu capture of
-# a one-step launch of k_batch<128> at a 128 x 128 tile (5.949 GB algorithmic;
-# profiles/batch_ensemble_d2q9_fp32.md); None for other tiles or when the kernel changes.
-ENSEMBLE_TRAFFIC_BYTES_PER_STEP = 6.1217e9
+# DRAM bytes (read + write) of one step of the 512-domain ensemble per work-item shape,
+# from one ncu capture of a one-step launch of k_batch (5.949 GB algorithmic;
+# profiles/batch_ensemble_d2q9_fp32.md); None for other shapes or when the kernel changes.
+ENSEMBLE_TRAFFIC_BYTES_PER_STEP = {(128, 256): 6.0412e9}
 WORKLOAD = "droplet Laplace sweep: 9 x 1024^2 D2Q9 thermal, FP32"
 
 
@@ -415,9 +415,9 @@ def run_ensemble(args):
                                "one persistent launch per call under a CUDA graph",
                    "nodes": N, "tile": {"w": tile[0], "h": tile[1], "autotuned": not args.tile}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": (ENSEMBLE_TRAFFIC_BYTES_PER_STEP / 1e9
-                                 if len(sizes) == 512 and tuple(tile) == (128, 128) else None),
-                     "traffic_unit": "GB per step (ncu, one-step launch, 128 x 128 tile)",
+                     "traffic": (ENSEMBLE_TRAFFIC_BYTES_PER_STEP[tuple(tile)] / 1e9
+                                 if len(sizes) == 512 and tuple(tile) in ENSEMBLE_TRAFFIC_BYTES_PER_STEP else None),
+                     "traffic_unit": "GB per step (ncu, one-step launch)",
                      "note": f"{BYTES_PER_LU} algorithmic B/LU; peak {peak_kind}"},
         "clocks": clk.summary(), "gpu_launches": 1, "finite": n_finite == len(sizes),
         "finite_domains": f"{n_finite}/{len(sizes)}",

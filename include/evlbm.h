@@ -294,15 +294,20 @@ int lbm_batch_step(lbm_batch *b, int n_steps);
  * (host FP64; any may be NULL).  Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */
 int lbm_batch_moments(lbm_batch *b, int domain, double *rho, double *u, double *T);
 
-/* Launch shape of the work items (as lbm_set_tile: tile_w in 64, 96, 128, 192,
- * tile_h >= 1; LBM_TILE_BALANCED does not apply, the persistent launch already takes
- * items as CTAs free up).  Errors: LBM_EINVAL. */
+/* Launch shape of the work items: strips of tile_w columns (64, 96, 128, 192) and,
+ * per domain, rows split into equal chunks of at most tile_h rows (>= 1; each chunk
+ * an even number of rows).  LBM_TILE_BALANCED does not apply: the persistent launch
+ * already hands out items as CTAs free up.  Errors: LBM_EINVAL. */
 int lbm_batch_set_tile(lbm_batch *b, int tile_w, int tile_h);
 int lbm_batch_get_tile(const lbm_batch *b, int *tile_w, int *tile_h);
 
-/* Autotuner: times every launch shape for probe_steps single-step launches that
- * read the current state and write the spare buffer (state unchanged); keeps
- * the fastest.  Errors: LBM_EINVAL, LBM_ECUDA, LBM_ETIMEOUT. */
+/* Autotuner: times every launch shape on one persistent launch of 2 * probe_steps
+ * steps from a device copy of the current state (steps overlap inside a launch as
+ * in a run), restoring the state before each probe and at the end; keeps the
+ * fastest.  The copy takes as much device memory as the populations of one buffer
+ * set, for the duration of the call; if it cannot be allocated, each shape is timed
+ * on probe_steps single-step launches into the spare buffer instead.  The state is
+ * unchanged either way.  Errors: LBM_EINVAL, LBM_ECUDA, LBM_ETIMEOUT. */
 int lbm_batch_autotune(lbm_batch *b, int probe_steps, int *tile_w, int *tile_h);
 
 /* Failure detection: polls (>= 1) a step wait may spin before it gives up

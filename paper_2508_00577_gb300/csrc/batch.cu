@@ -256,7 +256,10 @@ int retile(lbm_batch *b)
     const int W = b->tile_w;
     for (int d = 0; d < b->n; ++d) {
         BatchDomain &D = b->dom[d];
-        int H = b->tile_h < D.ny ? b->tile_h : D.ny;
+        // Equal chunks of at most tile_h rows (even), so that no domain ends in a
+        // short chunk that pays the pipeline fill for a few rows.
+        const int Hmax = b->tile_h < D.ny ? b->tile_h : D.ny;
+        int H = (D.ny + (D.ny + Hmax - 1) / Hmax - 1) / ((D.ny + Hmax - 1) / Hmax);
         H += H & 1;
         D.H = H;
         D.strips = (D.nx + W - 1) / W;
@@ -546,23 +549,54 @@ int lbm_batch_autotune(lbm_batch *b, int probe_steps, int *tile_w, int *tile_h)
 {
     if (!b || probe_steps < 1) return LBM_EINVAL;
     const int heights[] = {32, 64, 128, 256};
+    // Each shape is timed on one persistent launch of 2 * probe_steps steps, as in a run,
+    // where the last items of a step overlap the first items of the next.  The launch
+    // starts from a copy of the current state; an even step count ends in the current
+    // buffer, which is restored from the copy before every probe and at the end.  If the
+    // copy cannot be allocated, each shape is timed on single-step launches into the spare
+    // buffer instead (state untouched).
+    const size_t pop = sizeof(float) * 9ULL * (size_t)b->nodes;
+    float *save_f = nullptr, *save_g = nullptr;
+    bool saved = cudaMalloc(&save_f, pop) == cudaSuccess &&
+                 (!b->P.thermal || cudaMalloc(&save_g, pop) == cudaSuccess);
+    if (!saved) {
+        cudaGetLastError();                   // clear the failed allocation
+        if (save_f) cudaFree(save_f);
+        save_f = nullptr;
+    }
+    auto copy_state = [&](bool restore) -> cudaError_t {
+        const int c = b->cur;
+        cudaError_t e = cudaMemcpyAsync(restore ? b->f[c] : save_f, restore ? save_f : b->f[c], pop,
+                                        cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess && b->P.thermal)
+            e = cudaMemcpyAsync(restore ? b->g[c] : save_g, restore ? save_g : b->g[c], pop,
+                                cudaMemcpyDeviceToDevice, b->stream);
+        return e;
+    };
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
     float best = 1e30f;
     int bw = b->tile_w, bh = b->tile_h;
     int rc = LBM_OK;
+    const bool have_copy = saved && copy_state(false) == cudaSuccess;
+    if (saved && !have_copy) rc = LBM_ECUDA;
     for (int wi = 0; wi < evlbm::kFusedWidthCount && rc == LBM_OK; ++wi) {
         for (int hi = 0; hi < 4 && rc == LBM_OK; ++hi) {
             b->tile_w = evlbm::kFusedWidths[wi];
             b->tile_h = heights[hi];
             if ((rc = retile(b))) break;
-            // Probes run one step at a time from the current state into the spare
-            // buffer (no parity change), so the state is untouched.
             float ms = 0.f;
-            for (int s = 0; s <= probe_steps && rc == LBM_OK; ++s) {
-                if (s == 1 && cudaEventRecord(e0, b->stream) != cudaSuccess) rc = LBM_ECUDA;
-                if (rc == LBM_OK && enqueue(b, 1) != cudaSuccess) rc = LBM_ECUDA;
+            if (saved) {
+                if (copy_state(true) != cudaSuccess || cudaEventRecord(e0, b->stream) != cudaSuccess ||
+                    enqueue(b, 2 * probe_steps) != cudaSuccess)
+                    rc = LBM_ECUDA;
+            } else {
+                // Single steps from the current state into the spare buffer (no parity change).
+                for (int s = 0; s <= probe_steps && rc == LBM_OK; ++s) {
+                    if (s == 1 && cudaEventRecord(e0, b->stream) != cudaSuccess) rc = LBM_ECUDA;
+                    if (rc == LBM_OK && enqueue(b, 1) != cudaSuccess) rc = LBM_ECUDA;
+                }
             }
             if (rc == LBM_OK && cudaEventRecord(e1, b->stream) != cudaSuccess) rc = LBM_ECUDA;
             if (rc == LBM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = LBM_ECUDA;
@@ -577,6 +611,12 @@ int lbm_batch_autotune(lbm_batch *b, int probe_steps, int *tile_w, int *tile_h)
                 bh = b->tile_h;
             }
         }
+    }
+    if (saved) {
+        if (have_copy && (copy_state(true) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess))
+            if (rc == LBM_OK) rc = LBM_ECUDA;
+        cudaFree(save_f);
+        if (save_g) cudaFree(save_g);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
