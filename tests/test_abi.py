@@ -175,3 +175,12 @@ def test_surrogate_rejects_invalid_arguments_on_host():
         with pytest.raises(S.SurError) as e:
             S.sur_gemm(c, 16)
         assert e.value.code == S.SUR_EINVAL
+
+
+def test_binding_constants_match_header():
+    """Every LBM_* constant the header defines has the same value in the binding."""
+    text = open(HEADER).read()
+    defs = dict(re.findall(r"^#define\s+(LBM_\w+)\s+\(?(-?\d+)\)?", text, re.M))
+    assert {"LBM_OK", "LBM_EINVAL", "LBM_TILE_BALANCED", "LBM_FP32", "LBM_EOS_CS"} <= set(defs)
+    for name, value in defs.items():
+        assert getattr(ev, name) == int(value), name
