@@ -184,3 +184,13 @@ def test_binding_constants_match_header():
     assert {"LBM_OK", "LBM_EINVAL", "LBM_TILE_BALANCED", "LBM_FP32", "LBM_EOS_CS"} <= set(defs)
     for name, value in defs.items():
         assert getattr(ev, name) == int(value), name
+
+
+def test_surrogate_binding_constants_match_header():
+    """Every SUR_* enumerator of the surrogate header has the same value in the binding."""
+    from paper_2508_00577_gb300 import surrogate as S
+    text = open(SUR_HEADER).read()
+    vals = dict(re.findall(r"\b(SUR_[A-Z0-9_]+)\s*=\s*(\d+)", text))
+    assert len(vals) >= 18
+    for name, value in vals.items():
+        assert getattr(S, name) == int(value), name
