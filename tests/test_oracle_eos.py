@@ -111,3 +111,49 @@ def test_interface_width_and_tension_scale():
     w4, s4 = E.interface(eos, a, b, 0.8 * Tc, 4.0)
     assert w4 / w1 == pytest.approx(2.0, rel=1e-6)
     assert s4 / s1 == pytest.approx(2.0, rel=1e-6)
+
+
+@pytest.mark.parametrize("eos,a,b", CASES)
+def test_free_energy_chemical_potential_and_pressure_are_consistent(eos, a, b):
+    """Helmholtz free-energy density f(rho) at fixed T: mu = df/drho and dp/drho =
+    rho dmu/drho (central differences), and the Euler relation p = rho mu - f; checked
+    over vapour, spinodal and liquid densities at T/Tc = 0.8."""
+    rc, Tc = E.critical_point(eos, a, b)
+    RT = 0.8 * Tc
+    for rho in (0.05 * rc, 0.5 * rc, rc, 1.8 * rc, 2.4 * rc):
+        h = 1e-5 * rho
+        f = lambda r: float(E.free_energy(eos, a, b, RT, r))
+        mu = lambda r: float(E.chem_potential(eos, a, b, RT, r))
+        p = float(E.pressure(eos, a, b, RT, rho))
+        assert (f(rho + h) - f(rho - h)) / (2 * h) == pytest.approx(mu(rho), rel=1e-8, abs=1e-10 * RT)
+        assert rho * (mu(rho + h) - mu(rho - h)) / (2 * h) == pytest.approx(
+            float(E.dp_drho(eos, a, b, RT, rho)), rel=1e-6, abs=1e-9 * RT)
+        assert rho * mu(rho) - f(rho) == pytest.approx(p, rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("eos,a,b", CASES)
+def test_grand_excess_vanishes_at_coexistence_and_is_positive_between(eos, a, b):
+    _, Tc = E.critical_point(eos, a, b)
+    RT = 0.8 * Tc
+    rv, rl = E.maxwell(eos, a, b, RT)
+    om = E.grand_excess(eos, a, b, RT, np.array([rv, rl]), rv, rl)
+    scale = float(E.pressure(eos, a, b, RT, rl))
+    assert np.all(np.abs(om) <= 1e-10 * max(scale, RT * rl))
+    mid = np.linspace(rv, rl, 101)[1:-1]
+    assert np.all(E.grand_excess(eos, a, b, RT, mid, rv, rl) > 0)
+
+
+def test_interface_on_a_quartic_well_matches_the_tanh_closed_forms(monkeypatch):
+    """Square-gradient theory on a double well omega = A (rho - rv)^2 (rl - rho)^2 has the
+    profile rho = mid + (rl - rv)/2 tanh(x / xi), xi = sqrt(2 kappa / A) / (rl - rv), so
+    the 10-90 % width is 2 xi artanh(0.8) and sigma = (rl - rv)^3 sqrt(2 kappa A) / 6.
+    The oracle's interface() is run with its coexistence and excess grand potential
+    replaced by this well, and must reproduce both closed forms."""
+    rv, rl, A, kappa = 0.2, 1.4, 3.0, 0.7
+    monkeypatch.setattr(E, "maxwell", lambda *args, **kw: (rv, rl))
+    monkeypatch.setattr(E, "grand_excess",
+                        lambda eos, a, b, RT, rho, v, l: A * (np.asarray(rho) - v) ** 2 * (l - np.asarray(rho)) ** 2)
+    width, sigma = E.interface(E.CS, 0.1, 4.0, 0.01, kappa)
+    xi = np.sqrt(2.0 * kappa / A) / (rl - rv)
+    assert width == pytest.approx(2.0 * xi * np.arctanh(0.8), rel=2e-5)
+    assert sigma == pytest.approx((rl - rv) ** 3 * np.sqrt(2.0 * kappa * A) / 6.0, rel=1e-8)
