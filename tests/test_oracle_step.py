@@ -292,3 +292,29 @@ def test_dense_gas_sound():
     rh = np.array(rhohat)
     zc = np.where(np.diff(np.sign(rh)) != 0)[0]
     assert 2 * math.pi / (2.0 * np.mean(np.diff(zc))) / k == pytest.approx(cs, rel=0.01)
+
+
+@pytest.mark.parametrize("Q", [9, 27])
+@pytest.mark.parametrize("thermal", [1, 0])
+@pytest.mark.parametrize("u0", [(0.0, 0.0, 0.0), (0.03, -0.02, 0.01)])
+def test_uniform_state_is_a_fixed_point(Q, thermal, u0):
+    """A uniform state (liquid density of the non-ideal fluid, at rest or moving) has
+    no gradients: F = 0 (Eq. EVforce1), Phi = Phi' = q' = 0, so f* = f^eq, g* = g^eq and
+    the collision of Eq. pre_LBM leaves the equilibria unchanged; streaming moves equal
+    values.  The populations stay at their initial values to rounding, and the
+    macroscopic fields are returned unchanged."""
+    RT, rv, rl, kappa = cs_state(0.8)
+    nx, ny, nz = 6, 5, (4 if Q == 27 else 1)
+    N = nx * ny * nz
+    D = 2 if Q == 9 else 3
+    p = oracle.Params(Q=Q, nx=nx, ny=ny, nz=nz, eos=E.CS, a=CS_A, b=CS_B, kappa=kappa, tau=0.3, thermal=thermal)
+    u = np.array([np.full(N, u0[a]) for a in range(D)])
+    s = oracle.State(p, np.full(N, rl), u, np.full(N, RT))
+    f0, g0 = s.f.copy(), s.g.copy()
+    s.step(10)
+    assert np.max(np.abs(s.f - f0)) <= 1e-14 * np.max(np.abs(f0))
+    if thermal:
+        assert np.max(np.abs(s.g - g0)) <= 1e-14 * np.max(np.abs(g0))
+    rho, uu, T, F = s.macro()
+    assert np.allclose(rho, rl, rtol=1e-14) and np.allclose(T, RT, rtol=1e-13)
+    assert np.allclose(uu, u, atol=1e-15) and np.all(np.abs(F) <= 1e-15)
