@@ -318,3 +318,55 @@ def test_uniform_state_is_a_fixed_point(Q, thermal, u0):
     rho, uu, T, F = s.macro()
     assert np.allclose(rho, rl, rtol=1e-14) and np.allclose(T, RT, rtol=1e-13)
     assert np.allclose(uu, u, atol=1e-15) and np.all(np.abs(F) <= 1e-15)
+
+
+def _perm_fields(rho, u, T, n, D, op):
+    """Apply an axis permutation or reflection of the cubic (square) lattice to fields
+    stored [z][y][x]: op = 'xy' swaps x and y, 'xz' swaps x and z, 'rx' reflects x."""
+    shp = (n, n, n) if D == 3 else (1, n, n)
+
+    def f3(a):
+        a = a.reshape(shp)
+        if op == "xy":
+            a = np.swapaxes(a, 1, 2)
+        elif op == "xz":
+            a = np.swapaxes(a, 0, 2)
+        else:
+            a = np.roll(a[:, :, ::-1], 1, axis=2)              # x -> -x (mod n)
+        return np.ascontiguousarray(a).reshape(-1)
+
+    uu = [f3(u[a]) for a in range(D)]
+    if op == "xy":
+        uu[0], uu[1] = uu[1], uu[0]
+    elif op == "xz":
+        uu[0], uu[2] = uu[2], uu[0]
+    else:
+        uu[0] = -uu[0]
+    return f3(rho), np.array(uu), f3(T)
+
+
+@pytest.mark.parametrize("Q,op", [(9, "xy"), (9, "rx"), (27, "xy"), (27, "xz"), (27, "rx")])
+def test_step_commutes_with_the_lattice_symmetries(Q, op):
+    """The velocity sets, stencils and equilibria are invariant under the permutations
+    and reflections of the axes, so stepping a transformed state gives the transformed
+    result (to rounding): an index or sign slip on one axis breaks this."""
+    RT, rv, rl, kappa = cs_state(0.85)
+    n = 6 if Q == 27 else 10
+    D = 3 if Q == 27 else 2
+    N = n ** D
+    s1, s2 = E.spinodal(E.CS, CS_A, CS_B, RT)
+    rho = inputs.spinodal_noise(n, n, n if D == 3 else 1, 0.5 * (s1 + s2), RT, amplitude=0.05, D=D)[0]
+    r = np.random.default_rng(3)
+    u = 0.01 * r.standard_normal((D, N))
+    T = RT * (1.0 + 0.02 * r.standard_normal(N))
+    p = oracle.Params(Q=Q, nx=n, ny=n, nz=n if D == 3 else 1, eos=E.CS, a=CS_A, b=CS_B, kappa=kappa, tau=0.3)
+    a = oracle.State(p, rho, u, T)
+    a.step(5)
+    ra, ua, Ta, _ = a.macro()
+    b = oracle.State(p, *_perm_fields(rho, u, T, n, D, op))
+    b.step(5)
+    rb, ub, Tb, _ = b.macro()
+    pr, pu, pT = _perm_fields(ra, ua, Ta, n, D, op)
+    assert np.max(np.abs(rb - pr) / pr) <= 1e-12
+    assert np.max(np.abs(Tb - pT) / pT) <= 1e-12
+    assert np.max(np.abs(ub - pu)) <= 1e-13
