@@ -175,8 +175,12 @@ long long lbm_bounds_violations(void);
  * Errors: LBM_EINVAL (NULL arguments, not a checkpoint of this library, another
  * version, or parameters or sizes that differ from the context's; the message
  * names the field), LBM_EIO (the file cannot be opened, written or read, or is
- * truncated), LBM_ENOMEM (host staging buffer), LBM_ECUDA.  On an error lbm_load
- * may have overwritten part of the state. */
+ * truncated), LBM_ENOMEM (host staging buffer), LBM_ECUDA.  lbm_load reads the
+ * populations into the context's spare buffers and the frozen R T field into host
+ * memory, and switches the context over only after every section has been read:
+ * after an LBM_EINVAL, LBM_EIO or LBM_ENOMEM the state and step count are those
+ * from before the call (it needs host memory for the frozen R T field, 4 or 8
+ * bytes per node, when thermal = 0). */
 int lbm_save(lbm_ctx *ctx, const char *path);
 int lbm_load(lbm_ctx *ctx, const char *path);
 
@@ -255,7 +259,10 @@ int lbm_interface(int eos, double a, double b, double RT, double kappa, double o
  * the library until the process exits); larger lattices return LBM_EINVAL.  It
  * calls no cudaMalloc, cudaFree or other allocating routine.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress) with
- * the device current; make that first call before any stream capture.  All
+ * the device current; make that first call before any stream capture.  The
+ * address is kept for the life of the process: after cudaDeviceReset (which
+ * unloads the library's device code) further calls are unsupported unless the
+ * library is unloaded and loaded again.  All
  * calls share the one array, so calls whose kernels overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller.  The
  * populations are bit-identical to lbm_step on an LBM_FP64 context.

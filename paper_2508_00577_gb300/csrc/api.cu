@@ -728,27 +728,44 @@ int lbm_load(lbm_ctx *c, const char *path)
         fclose(fp);
         return fail(c, LBM_EIO, "lbm_load: %s is truncated or has trailing bytes (%zu expected)", path, total);
     }
+    // The populations and reference states go to the spare buffers and the frozen R T
+    // field to host memory; only when every section has been read does the context
+    // switch to them, so a failed load leaves the state as it was.
+    void *dst[3] = {c->f[c->cur ^ 1], c->g[c->cur ^ 1], c->R[c->cur ^ 1]};
     size_t largest = 0;
-    for (int k = 0; k < 4; ++k) largest = L.bytes[k] > largest ? L.bytes[k] : largest;
+    for (int k = 0; k < 3; ++k) largest = L.bytes[k] > largest ? L.bytes[k] : largest;
     const size_t chunk = largest < kCkChunk ? largest : kCkChunk;
     unsigned char *buf = chunk ? static_cast<unsigned char *>(malloc(chunk)) : nullptr;
+    unsigned char *rt = L.bytes[3] ? static_cast<unsigned char *>(malloc(L.bytes[3])) : nullptr;
     int rc = LBM_OK;
-    if (chunk && !buf) rc = fail(c, LBM_ENOMEM, "lbm_load: host staging buffer");
-    CK(c, cudaStreamSynchronize(c->stream));
-    for (int k = 0; k < 4 && rc == LBM_OK; ++k)
+    if ((chunk && !buf) || (L.bytes[3] && !rt)) rc = fail(c, LBM_ENOMEM, "lbm_load: host staging buffer");
+    if (rc == LBM_OK) {
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "lbm_load");
+    }
+    for (int k = 0; k < 3 && rc == LBM_OK; ++k)
         for (size_t o = 0; o < L.bytes[k] && rc == LBM_OK; o += chunk) {
             const size_t n = L.bytes[k] - o < chunk ? L.bytes[k] - o : chunk;
             if (fread(buf, 1, n, fp) != n) {
                 rc = fail(c, LBM_EIO, "lbm_load: read failed");
                 break;
             }
-            cudaError_t e = cudaMemcpyAsync(static_cast<char *>(L.dev[k]) + o, buf, n, cudaMemcpyHostToDevice,
+            cudaError_t e = cudaMemcpyAsync(static_cast<char *>(dst[k]) + o, buf, n, cudaMemcpyHostToDevice,
                                             c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) rc = cuda_fail(c, e, "lbm_load");
         }
+    if (rc == LBM_OK && L.bytes[3] && fread(rt, 1, L.bytes[3], fp) != L.bytes[3])
+        rc = fail(c, LBM_EIO, "lbm_load: read failed");
+    if (rc == LBM_OK && L.bytes[3]) {
+        cudaError_t e = cudaMemcpyAsync(L.dev[3], rt, L.bytes[3], cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "lbm_load");
+    }
     free(buf);
+    free(rt);
     fclose(fp);
+    if (rc == LBM_OK) c->cur ^= 1;
     if (rc == LBM_OK) c->steps = steps;
     return rc;
 }

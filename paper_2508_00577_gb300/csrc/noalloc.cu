@@ -13,6 +13,8 @@
 // populations are bit-identical to lbm_step on an FP64 context.
 #include <string.h>
 
+#include <atomic>
+
 #include "../../include/evlbm.h"
 #include "ref_launch.cuh"
 
@@ -25,7 +27,10 @@ constexpr long long kNoallocMaxNodes = 32768;
 static __device__ __align__(256) double g_noalloc_scratch[evlbm::kRefFieldCount * kNoallocMaxNodes];
 
 constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices];   // device address of g_noalloc_scratch per device (set-up once)
+// Device address of g_noalloc_scratch per device, looked up once.  Atomic because two
+// threads may make their first call on a device at the same time (both store the same
+// address).  A device reset unloads the module, so the address is not valid afterwards.
+std::atomic<void *> g_scratch_addr[kMaxDevices];
 
 }  // namespace
 
@@ -50,10 +55,10 @@ extern "C" int lbm_step_noalloc(const lbm_params *p, const double *d_f, const do
     // __device__ array is not a device address, so ask the runtime for it.
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ECUDA;
-    if (!g_scratch_addr[dev]) {
-        void *addr = nullptr;
-        if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return LBM_ECUDA;
-        g_scratch_addr[dev] = addr;
+    void *scratch = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!scratch) {
+        if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess || !scratch) return LBM_ECUDA;
+        g_scratch_addr[dev].store(scratch, std::memory_order_release);
     }
 
     evlbm::KParams k;
@@ -76,9 +81,9 @@ extern "C" int lbm_step_noalloc(const lbm_params *p, const double *d_f, const do
     // it is read, so the stale contents of the previous call need no clearing.
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = p->lattice == LBM_D2Q9
-                        ? evlbm::ref_step_t<double, double, 9>(k, g_scratch_addr[dev], d_RT, d_f, d_g, d_f_out,
+                        ? evlbm::ref_step_t<double, double, 9>(k, scratch, d_RT, d_f, d_g, d_f_out,
                                                                d_g_out, nullptr, nullptr, st)
-                        : evlbm::ref_step_t<double, double, 27>(k, g_scratch_addr[dev], d_RT, d_f, d_g, d_f_out,
+                        : evlbm::ref_step_t<double, double, 27>(k, scratch, d_RT, d_f, d_g, d_f_out,
                                                                 d_g_out, nullptr, nullptr, st);
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
