@@ -130,6 +130,22 @@ def rel_rho_err(o, g):
     return np.max(np.abs(rg - ro) / ro)
 
 
+def field_errs(o, g):
+    """(max |d rho|/rho, max |d T|/T, max |d u|) of the GPU state against the oracle's,
+    every node, the fields as the next step computes them."""
+    ro, uo, To = o.macro()[:3]
+    rg, ug, Tg, _ = g.moments()
+    return (float(np.max(np.abs(rg - ro) / ro)), float(np.max(np.abs(Tg - To) / To)),
+            float(np.max(np.abs(ug.reshape(uo.shape) - uo))))
+
+
+def assert_fields(o, g, tol):
+    """rho and T within `tol` relative, u within tol/10 absolute: the lattice velocity
+    scale is the sound speed sqrt(theta0) ~ 0.1, so tol/10 is the same relative bound."""
+    er, eT, eu = field_errs(o, g)
+    assert er <= tol and eT <= tol and eu <= 0.1 * tol, (er, eT, eu)
+
+
 @pytest.mark.parametrize("nx,ny,nz", [(96, 80, 1), (130, 70, 2), (257, 33, 1), (7, 5, 1), (1, 1, 1), (300, 260, 1)])
 def test_fp32_d2q9(nx, ny, nz):
     """FP32 (fused single-pass kernel for D2Q9): max |d rho|/rho <= 1e-5 over 50 steps
@@ -138,13 +154,13 @@ def test_fp32_d2q9(nx, ny, nz):
     tails and degenerate 1-node lattices."""
     fields, kappa = droplet_fields(nx, ny, nz)
     o, g = pair(9, nx, ny, nz, fields, kappa, ev.LBM_FP32)
-    assert rel_rho_err(o, g) <= 1e-6
+    assert_fields(o, g, 1e-6)
     o.step(1)
     g.step(1)
-    assert rel_rho_err(o, g) <= 1e-6
+    assert_fields(o, g, 1e-6)
     o.step(49)
     g.step(49)
-    assert rel_rho_err(o, g) <= 1e-5
+    assert_fields(o, g, 1e-5)
 
 
 @pytest.mark.parametrize("thermal", [1, 0])
@@ -167,7 +183,7 @@ def test_fp32_d3q27(nx, ny, nz, hz, thermal):
         assert ev.lbm_launches_per_step(g.ctx) == 1       # the fused kernel, not the stage kernels
         o.step(10)
         g.step(10)
-        assert rel_rho_err(o, g) <= 1e-5
+        assert_fields(o, g, 1e-5)
 
 
 @pytest.mark.parametrize("lam", [0.5, 2.0])
@@ -187,7 +203,7 @@ def test_general_lambda(lam):
             if prec == ev.LBM_FP64:
                 assert_bitexact(o, g)
             else:
-                assert rel_rho_err(o, g) <= 1e-5
+                assert_fields(o, g, 1e-5)
     _, Tc = E.critical_point(E.CS, A, B)
     RT = 0.85 * Tc
     s1, s2 = E.spinodal(E.CS, A, B, RT)
@@ -204,7 +220,7 @@ def test_general_lambda(lam):
             if prec == ev.LBM_FP64:
                 assert_bitexact(o3, g)
             else:
-                assert rel_rho_err(o3, g) <= 1e-5
+                assert_fields(o3, g, 1e-5)
 
 
 @pytest.mark.parametrize("Q", [9, 27])
@@ -232,7 +248,7 @@ def test_fp32_vdw_eos_and_literal_force(Q, variant):
     with g:
         o.step(steps)
         g.step(steps)
-        assert rel_rho_err(o, g) <= 1e-5
+        assert_fields(o, g, 1e-5)
 
 
 @pytest.mark.parametrize("nx,ny", [(64, 48), (300, 40)])
@@ -241,7 +257,7 @@ def test_fp32_d2q9_isothermal(nx, ny):
     o, g = pair(9, nx, ny, 1, fields, kappa, ev.LBM_FP32, thermal=0)
     o.step(50)
     g.step(50)
-    assert rel_rho_err(o, g) <= 1e-5
+    assert_fields(o, g, 1e-5)
 
 
 @pytest.mark.parametrize("precision", [ev.LBM_FP16_DEV, ev.LBM_BF16_DEV])
@@ -251,8 +267,7 @@ def test_reduced_precision_d2q9(precision, nx, ny, nz):
     o, g = pair(9, nx, ny, nz, fields, kappa, precision)
     o.step(100)
     g.step(100)
-    err = rel_rho_err(o, g)
-    assert err <= TOL[precision], err
+    assert_fields(o, g, TOL[precision])
 
 
 def test_fp32_long_run_droplet():
