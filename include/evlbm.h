@@ -60,11 +60,13 @@ extern "C" {
 
 #define LBM_FP64 0           /* FP64 storage and arithmetic (bit-exact reference order) */
 #define LBM_FP32 1           /* FP32 storage and arithmetic */
-/* 16-bit storage: each population is stored as its deviation from the local
- * equilibrium of the node that wrote it, scaled by its weight,
+/* 16-bit storage: each population is stored in FP16 or BF16 as its deviation from
+ * the local equilibrium (Eqs. feq, geq) of the node that wrote it, scaled by its
+ * weight,
  *   (h_i - h_i^eq(R)) / (w_i rho_R)   (g: / (w_i rho_R 3/2 RT_R)),
- * with that node's reference state R = (rho, u, theta0, RT) stored beside the
- * populations in the same format; arithmetic is FP32. */
+ * with that node's reference state R = (rho, u, theta0, 3/2 RT) stored beside the
+ * populations as an FP32 record of 24 bytes per node; arithmetic is FP32.  D3Q27
+ * runs the fused single-pass kernel, D2Q9 the stage kernels. */
 #define LBM_FP16_DEV 2       /* FP16 deviation storage */
 #define LBM_BF16_DEV 3       /* BF16 deviation storage */
 
@@ -153,7 +155,7 @@ long long lbm_bounds_violations(void);
 
 /* Checkpoint and resume.  The method has no state beyond the post-collision
  * populations of Eq. (pre_LBM) (plus, per storage type, the per-node reference
- * states of 16-bit deviation storage and the frozen R T field when thermal = 0),
+ * records of 16-bit deviation storage and the frozen R T field when thermal = 0),
  * so a checkpoint holds exactly those device buffers, byte for byte in the
  * context's own storage format, with the step count and every lbm_params field:
  * a resumed run is bit-identical to one that never stopped.
@@ -161,7 +163,7 @@ long long lbm_bounds_violations(void);
  * lbm_save writes `path` (first to "<path>.tmp", then renamed over `path`, so an
  * interrupted save never leaves a partial file under the final name).  It waits
  * for the work queued on the context's stream.  Layout (little-endian): the
- * 8 bytes "EVLBMCKP", u32 version (1), u32 0, i32 lattice nx ny nz eos thermal
+ * 8 bytes "EVLBMCKP", u32 version (2), u32 0, i32 lattice nx ny nz eos thermal
  * precision force_form, f64 a b R kappa tau lambda, i64 step count, u64 byte
  * counts of the four sections (f, g, reference states, frozen R T; 0 when
  * absent), then the sections in that order.  The host is staged through a
@@ -185,11 +187,27 @@ int lbm_save(lbm_ctx *ctx, const char *path);
 int lbm_load(lbm_ctx *ctx, const char *path);
 
 /* Number of kernel launches one lbm_step time step enqueues for this context
- * (1 for the fused single-pass kernel, 4 for the stage-by-stage kernels);
+ * (1 for the fused single-pass kernels: D2Q9 FP32 and D3Q27 FP32, FP16_DEV and
+ * BF16_DEV, divergence force form; 4 for the stage-by-stage kernels, 5 with walls);
  * -1 for NULL. */
 int lbm_launches_per_step(const lbm_ctx *ctx);
 
-/* Launch shape of the fused single-pass kernels (used at FP32).  D3Q27: tile_w = 16
+/* Walls, for the thermal Couette flow of the paper's validation (u and T prescribed at
+ * x = 0 and x = L_x; the paper does not state its wall scheme).  With enable = 1 the
+ * lattice columns x = 0 and x = nx-1 become wall nodes: they do not stream (their moments
+ * are those of their own populations), carry no force and do not collide; after every
+ * step their populations are the equilibria f^eq(rho_a, u_w, theta0(rho_a, R T_w)) and
+ * g^eq(rho_a, u_w, R T_w) of Eqs. feq and geq, with rho_a the density of the fluid node
+ * next to them in x at that step and u_w = u_lo (x = 0) or u_hi (x = nx-1).  The channel
+ * width between the wall nodes is nx - 1.  The initial fields given to lbm_init should
+ * hold u_w and T_w on the wall columns already.  The walls move parallel to themselves
+ * (u_x = 0; u_z = 0 on D2Q9).  Requires kappa = 0 (a single-phase fluid: the capillary
+ * stress of a wall node would reach through the periodic x boundary), nx >= 3 and FP64 or
+ * FP32 storage.  enable = 0 restores periodic x (u_lo, u_hi may then be NULL).
+ * Errors: LBM_EINVAL. */
+int lbm_set_walls(lbm_ctx *ctx, int enable, const double u_lo[3], const double u_hi[3], double T_w);
+
+/* Launch shape of the fused single-pass kernels.  D3Q27: tile_w = 16
  * (16 x 16 columns per CTA) and tile_h = the z-chunk a CTA marches through (>= 1).
  * D2Q9: strips of
  * tile_w columns (one of 64, 96, 128, 192) marching over chunks of tile_h rows
@@ -255,7 +273,7 @@ int lbm_interface(int eos, double a, double b, double RT, double kappa, double o
  * device), d_RT (the frozen R*T field [N], read only when thermal = 0; d_g and
  * d_g_out are ignored then) and d_f_out, d_g_out (output populations; must not
  * alias the inputs).  The intermediate fields live in a static array inside the
- * library sized for at most 32768 nodes (7.5 MiB, held on every GPU that loads
+ * library sized for at most 32768 nodes (7.75 MiB, held on every GPU that loads
  * the library until the process exits); larger lattices return LBM_EINVAL.  It
  * calls no cudaMalloc, cudaFree or other allocating routine.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress) with

@@ -47,6 +47,9 @@ class orc_params(ctypes.Structure):
         ("lambda_", ctypes.c_double),
         ("thermal", ctypes.c_int),
         ("force_form", ctypes.c_int),
+        ("walls", ctypes.c_int),
+        ("wall_u", (ctypes.c_double * 3) * 2),
+        ("wall_RT", ctypes.c_double),
     ]
 
 
@@ -127,10 +130,13 @@ class Params:
     """Model parameters (the paper's lattice, EOS constants a, b, R, kappa, tau, lambda)."""
 
     def __init__(self, Q=9, nx=64, ny=64, nz=1, eos=1, a=1.0, b=4.0, R=1.0, kappa=0.0,
-                 tau=0.3, lambda_=1.0, thermal=1, force_form=0):
+                 tau=0.3, lambda_=1.0, thermal=1, force_form=0, walls=None):
+        """walls: None (periodic), or (u_lo, u_hi, T_w): the columns x = 0 and x = nx-1 are
+        wall nodes moving with the velocities u_lo, u_hi (3-vectors) at temperature T_w."""
         self.Q, self.nx, self.ny, self.nz = Q, nx, ny, nz
         self.eos, self.a, self.b, self.R, self.kappa = eos, a, b, R, kappa
         self.tau, self.lambda_, self.thermal, self.force_form = tau, lambda_, thermal, force_form
+        self.walls = walls
 
     @property
     def D(self):
@@ -141,8 +147,16 @@ class Params:
         return self.nx * self.ny * self.nz
 
     def c(self):
+        wu = ((ctypes.c_double * 3) * 2)()
+        wRT = 0.0
+        if self.walls is not None:
+            lo, hi, Tw = self.walls
+            for a in range(3):
+                wu[0][a], wu[1][a] = float(lo[a]), float(hi[a])
+            wRT = self.R * float(Tw)
         return orc_params(self.Q, self.nx, self.ny, self.nz, self.eos, self.a, self.b, self.R,
-                          self.kappa, self.tau, self.lambda_, self.thermal, self.force_form)
+                          self.kappa, self.tau, self.lambda_, self.thermal, self.force_form,
+                          1 if self.walls is not None else 0, wu, wRT)
 
 
 class State:

@@ -41,6 +41,9 @@ typedef struct {
     double lambda;    /* relaxation time of the shifted equilibrium */
     int thermal;      /* 1: f and g populations; 0: temperature frozen, g absent */
     int force_form;   /* 0: divergence (Korteweg stress) form; 1: literal grad(a rho^2) + kappa rho grad(lap rho) */
+    int walls;        /* 1: the columns x = 0 and x = nx-1 are wall nodes (see "Walls" below) */
+    double wall_u[2][3];  /* velocity of the wall at x = 0 and at x = nx-1 */
+    double wall_RT;   /* wall temperature R T_w */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -76,6 +79,29 @@ static long node_shift(const orc_params *p, long n, int dx, int dy, int dz)
     y = (y + dy + ny) % ny;
     z = (z + dz + nz) % nz;
     return x + nx * (y + ny * z);
+}
+
+/* Walls (the thermal Couette set-up of the paper's validation: u and T prescribed at
+ * x = 0 and x = L_x).  The paper does not state its wall scheme; the reading used here
+ * is a diffusely reflecting wall on the wall nodes.  With p->walls set, the lattice
+ * columns x = 0 and x = nx-1 are wall nodes.  A wall node
+ *   - does not stream: its moments, which the fluid nodes' stencils read, are those of
+ *     its own populations,
+ *   - carries no force (F = 0), so its moments are exactly (rho_w, u_w, R T_w),
+ *   - does not collide: it absorbs the populations that stream into it from the fluid
+ *     (mass m per step) and its populations become the equilibria
+ *     f^eq(rho_w, u_w, theta0(rho_w, R T_w)) and g^eq(rho_w, u_w, R T_w) (Eqs. feq, geq)
+ *     with rho_w such that the mass they send back into the fluid equals m: the
+ *     populations moving off a wall with u_x = 0 carry rho_w theta0 / 2 = P_E(rho_w) / 2,
+ *     so P_E(rho_w, R T_w) = 2 m (mass is conserved; energy is exchanged with the wall).
+ * Nothing crosses between the two walls through the periodic x boundary as long as
+ * kappa = 0 (the stress of a wall node then needs no density gradient). */
+static int is_wall(const orc_params *p, long n)
+{
+    if (!p->walls)
+        return 0;
+    long x = n % p->nx;
+    return x == 0 || x == p->nx - 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -253,6 +279,7 @@ typedef struct {
     double *rho, *j, *Gam;         /* raw moments */
     double *Pi, *lap, *A;          /* force intermediates */
     double *F, *u, *RT, *theta0, *P0, *gamma0, *flux, *wq;
+    double *m_in;                  /* mass streaming into each wall node this step */
 } work;
 
 static int work_alloc(const orc_params *p, work *W)
@@ -276,7 +303,8 @@ static int work_alloc(const orc_params *p, work *W)
     W->gamma0 = malloc(sizeof(double) * N);
     W->flux = malloc(sizeof(double) * 3 * N);
     W->wq = malloc(sizeof(double) * N);
-    if (!W->fs || !W->gs || !W->rho || !W->j || !W->Gam || !W->Pi || !W->lap || !W->A || !W->F ||
+    W->m_in = malloc(sizeof(double) * N);
+    if (!W->m_in ||!W->fs || !W->gs || !W->rho || !W->j || !W->Gam || !W->Pi || !W->lap || !W->A || !W->F ||
         !W->u || !W->RT || !W->theta0 || !W->P0 || !W->gamma0 || !W->flux || !W->wq)
         return -1;
     return 0;
@@ -286,7 +314,7 @@ static void work_free(work *W)
 {
     free(W->fs); free(W->gs); free(W->rho); free(W->j); free(W->Gam); free(W->Pi);
     free(W->lap); free(W->A); free(W->F); free(W->u); free(W->RT); free(W->theta0);
-    free(W->P0); free(W->gamma0); free(W->flux); free(W->wq);
+    free(W->P0); free(W->gamma0); free(W->flux); free(W->wq); free(W->m_in);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -305,7 +333,7 @@ static void force_stage(const orc_params *p, const lattice *L, work *W)
     if (p->force_form == 0) {
         /* Divergence form F_a = -d_b Pi_ab with the Korteweg stress
          * Pi_ab = (-a rho^2 - kappa rho lap rho - 1/2 kappa |grad rho|^2) delta_ab + kappa d_a rho d_b rho. */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= 4096)
         for (long n = 0; n < N; ++n) {
             double gr[3], rho = W->rho[n];
             for (int a = 0; a < D; ++a)
@@ -321,7 +349,7 @@ static void force_stage(const orc_params *p, const lattice *L, work *W)
                     W->Pi[(a * 3 + b) * N + n] = (a == b) ? s + t : t;
                 }
         }
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= 4096)
         for (long n = 0; n < N; ++n)
             for (int a = 0; a < D; ++a) {
                 double div = 0.0;
@@ -331,12 +359,12 @@ static void force_stage(const orc_params *p, const lattice *L, work *W)
             }
     } else {
         /* Literal form F = grad(a rho^2) + kappa rho grad(lap rho). */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= 4096)
         for (long n = 0; n < N; ++n) {
             W->lap[n] = lap_iso(p, L, W->rho, n);
             W->A[n] = p->a * W->rho[n] * W->rho[n];
         }
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= 4096)
         for (long n = 0; n < N; ++n)
             for (int a = 0; a < D; ++a)
                 W->F[a * N + n] = grad_iso(p, L, W->A, n, a) + p->kappa * W->rho[n] * grad_iso(p, L, W->lap, n, a);
@@ -355,19 +383,33 @@ static void macro_stages(const orc_params *p, const lattice *L, const double *f,
     const long N = W->N;
     const int Q = L->Q, D = L->D;
 
-    /* 1. Pull streaming: f_i(x) = f~_i(x - c_i)  (Eq. pre_LBM, exact on-lattice propagation). */
-#pragma omp parallel for schedule(static)
+    /* 1. Pull streaming: f_i(x) = f~_i(x - c_i)  (Eq. pre_LBM, exact on-lattice propagation).
+     *    Wall nodes keep their own populations (walls, below). */
+#pragma omp parallel for schedule(static) if (N >= 4096)
     for (long n = 0; n < N; ++n) {
         for (int i = 0; i < Q; ++i) {
-            long src = node_shift(p, n, -L->c[i][0], -L->c[i][1], -L->c[i][2]);
+            long src = is_wall(p, n) ? n : node_shift(p, n, -L->c[i][0], -L->c[i][1], -L->c[i][2]);
             W->fs[i * N + n] = f[i * N + src];
             if (p->thermal)
                 W->gs[i * N + n] = g[i * N + src];
         }
     }
 
+    /* Walls: the mass streaming into each wall node, sum over the populations moving
+     * toward it (c_x = -1 at x = 0, c_x = +1 at x = nx-1) pulled from the fluid. */
+    if (p->walls)
+        for (long n = 0; n < N; ++n) {
+            W->m_in[n] = 0.0;
+            if (!is_wall(p, n))
+                continue;
+            const int s = (n % p->nx) == 0 ? -1 : 1;
+            for (int i = 0; i < Q; ++i)
+                if (L->c[i][0] == s)
+                    W->m_in[n] = W->m_in[n] + f[i * N + node_shift(p, n, -L->c[i][0], -L->c[i][1], -L->c[i][2])];
+        }
+
     /* 2. Raw moments rho = sum f_i, j_a = sum c_ia f_i, Gamma = sum g_i  (ascending i). */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= 4096)
     for (long n = 0; n < N; ++n) {
         double rho = 0.0, j[3] = {0.0, 0.0, 0.0}, Gam = 0.0;
         for (int i = 0; i < Q; ++i) {
@@ -384,12 +426,17 @@ static void macro_stages(const orc_params *p, const lattice *L, const double *f,
         W->Gam[n] = Gam;
     }
 
-    /* 3. Non-local force in the Enskog gauge (stage above). */
+    /* 3. Non-local force in the Enskog gauge (stage above); none acts on wall nodes. */
     force_stage(p, L, W);
+    if (p->walls)
+        for (long n = 0; n < N; ++n)
+            if (is_wall(p, n))
+                for (int a = 0; a < D; ++a)
+                    W->F[a * N + n] = 0.0;
 
     /* 4.-5. Shifted velocity (Eq. u_shift), energy (double-population analogue of
      *       Eq. T_shift with Q~ = 0), temperature, EOS and the corrected fluxes. */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= 4096)
     for (long n = 0; n < N; ++n) {
         double rho = W->rho[n], u[3] = {0, 0, 0}, F[3] = {0, 0, 0};
         for (int a = 0; a < D; ++a) {
@@ -436,8 +483,10 @@ static void collide_stage(const orc_params *p, const lattice *L, work *W, double
     const double c_eq = 2.0 * beta;
     const double c_star = (1.0 / lambda) * (1.0 - beta);       /* (dt/lambda)(1 - beta) */
 
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= 4096)
     for (long n = 0; n < N; ++n) {
+        if (is_wall(p, n))
+            continue;
         double rho = W->rho[n], RT = W->RT[n], theta0 = W->theta0[n], P0 = W->P0[n];
         double u[3] = {0, 0, 0}, F[3] = {0, 0, 0};
         for (int a = 0; a < D; ++a) {
@@ -508,6 +557,55 @@ static void collide_stage(const orc_params *p, const lattice *L, work *W, double
     }
 }
 
+/* Density rho_w of a wall node at temperature RT with P_E(rho_w, RT) = P (P_E
+ * increases with rho): van der Waals form in closed form, rho = P / (RT + b P);
+ * Carnahan-Starling by sixteen Newton steps from the ideal-gas value P / RT, with
+ * dP_E/drho = RT d(eta Z)/d eta = RT (1 + 4 eta + 4 eta^2 - 4 eta^3 + eta^4)/(1 - eta)^4. */
+static double wall_density(const orc_params *p, double P, double RT)
+{
+    if (p->eos == 0)
+        return P / (RT + p->b * P);
+    double rho = P / RT;
+    for (int k = 0; k < 16; ++k) {
+        double eta = p->b * rho / 4.0;
+        double num = 1.0 + eta + eta * eta - eta * eta * eta;
+        double om = 1.0 - eta;
+        double Z = num / (om * om * om);
+        double dn = 1.0 + 4.0 * eta + 4.0 * eta * eta - 4.0 * eta * eta * eta + eta * eta * eta * eta;
+        rho = rho - (rho * RT * Z - P) / (RT * (dn / (om * om * om * om)));
+    }
+    return rho;
+}
+
+/* Wall nodes after the collision: equilibria at the wall velocity and temperature with
+ * the density that returns the absorbed mass (reading stated at is_wall). */
+static void wall_stage(const orc_params *p, const lattice *L, const work *W, double *f, double *g)
+{
+    const long N = W->N;
+    const long nx = p->nx;
+    for (long n = 0; n < N; ++n) {
+        if (!is_wall(p, n))
+            continue;
+        const long x = n % nx;
+        const int side = x == 0 ? 0 : 1;
+        double rho = wall_density(p, 2.0 * W->m_in[n], p->wall_RT), u[3], zeta[3] = {0, 0, 0}, out[27];
+        double P0, theta0, gamma0;
+        orc_eos(p->eos, p->thermal, p->b, rho, p->wall_RT, &P0, &theta0, &gamma0);
+        for (int a = 0; a < 3; ++a)
+            u[a] = a < L->D ? p->wall_u[side][a] : 0.0;
+        for (int a = 0; a < L->D; ++a)
+            zeta[a] = theta0 + u[a] * u[a];
+        prod_eq(L, rho, u, zeta, out);
+        for (int i = 0; i < L->Q; ++i)
+            f[i * N + n] = out[i];
+        if (p->thermal) {
+            geq_node(L, rho, u, theta0, p->wall_RT, out);
+            for (int i = 0; i < L->Q; ++i)
+                g[i * N + n] = out[i];
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Entry points                                                              */
 /* ------------------------------------------------------------------------ */
@@ -517,6 +615,8 @@ static int check(const orc_params *p)
     if (!p || (p->Q != 9 && p->Q != 27) || p->nx < 1 || p->ny < 1 || p->nz < 1)
         return -1;
     if (!(p->tau > 0.0) || !(p->lambda > 0.0))
+        return -1;
+    if (p->walls && (p->nx < 3 || p->kappa != 0.0 || !(p->wall_RT > 0.0)))
         return -1;
     return 0;
 }
@@ -531,7 +631,7 @@ int orc_init(const orc_params *p, const double *rho, const double *u, const doub
     lattice L;
     make_lattice(p->Q, &L);
     const long N = (long)p->nx * p->ny * p->nz;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= 4096)
     for (long n = 0; n < N; ++n) {
         double uu[3] = {0, 0, 0}, zeta[3] = {0, 0, 0}, out[27];
         double RT = p->R * T[n], P0, theta0, gamma0;
@@ -574,6 +674,8 @@ int orc_step(const orc_params *p, int nsteps, double *f, double *g, const double
     for (int s = 0; s < nsteps; ++s) {
         macro_stages(p, &L, f, g, RT_iso, &W);
         collide_stage(p, &L, &W, f, g);
+        if (p->walls)
+            wall_stage(p, &L, &W, f, g);
     }
     free(RT_iso);
     work_free(&W);

@@ -20,7 +20,7 @@ __all__ = [
     "lbm_get_tile", "lbm_autotune", "lbm_sync", "lbm_free",
     "lbm_last_error", "lbm_coexistence", "lbm_critical_point", "lbm_spinodal", "lbm_interface",
     "lbm_kappa_for_width", "lbm_step_noalloc", "lbm_reset_device",
-    "lbm_save", "lbm_load", "lbm_bounds_violations", "LBMError", "Lattice",
+    "lbm_save", "lbm_load", "lbm_bounds_violations", "lbm_set_walls", "LBMError", "Lattice",
     "LBM_D2Q9", "LBM_D3Q27", "LBM_TILE_BALANCED", "LBM_EOS_VDW", "LBM_EOS_CS", "LBM_FP64", "LBM_FP32",
     "LBM_FP16_DEV", "LBM_BF16_DEV", "EXPORTED_SYMBOLS", "Batch",
 ]
@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = (
     "lbm_spinodal", "lbm_interface", "lbm_step_noalloc", "lbm_batch_init", "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_tile",
     "lbm_batch_get_tile", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_batch_nodes",
     "lbm_batch_free", "lbm_batch_last_error", "lbm_reset_device", "lbm_save", "lbm_load",
-    "lbm_bounds_violations",
+    "lbm_bounds_violations", "lbm_set_walls",
 )
 
 
@@ -111,6 +111,7 @@ def lib():
             L.lbm_load.argtypes = [vp, ctypes.c_char_p]
             L.lbm_step_count.restype = ctypes.c_longlong
             L.lbm_launches_per_step.argtypes = [vp]
+            L.lbm_set_walls.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.c_double]
             ip = ctypes.POINTER(ctypes.c_int)
             L.lbm_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             L.lbm_get_tile.argtypes = [vp, ip, ip]
@@ -237,6 +238,19 @@ def lbm_load(ctx, path):
 
 def lbm_launches_per_step(ctx):
     return lib().lbm_launches_per_step(ctx)
+
+
+def lbm_set_walls(ctx, enable, u_lo=None, u_hi=None, T_w=0.0):
+    """Wall nodes at the columns x = 0 and x = nx-1 (velocities u_lo, u_hi, temperature T_w),
+    or periodic x again with enable = 0."""
+    if not enable:
+        _check(lib().lbm_set_walls(ctx, 0, None, None, 0.0), ctx)
+        return
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    lo[:len(u_lo)] = u_lo
+    hi[:len(u_hi)] = u_hi
+    _check(lib().lbm_set_walls(ctx, 1, _dptr(lo), _dptr(hi), float(T_w)), ctx)
 
 
 def lbm_set_tile(ctx, tile_w, tile_h):

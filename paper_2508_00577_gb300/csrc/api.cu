@@ -22,7 +22,7 @@ struct lbm_ctx {
     size_t pop_bytes;      // bytes per stored population
     size_t real_bytes;     // bytes per scratch value (8 for FP64, 4 otherwise)
     void *f[2], *g[2];
-    void *R[2];            // per-node reference states of 16-bit storage ([D + 3][N])
+    void *R[2];            // per-node reference records of 16-bit storage ([N] of 16 bytes)
     int cur;
     void *RT_iso;          // frozen R*T field (thermal = 0), in the scratch precision
     void *scratch;         // stage-kernel fields, allocated on first use
@@ -205,7 +205,7 @@ int lbm_init(const lbm_params *params, const double *rho, const double *u, const
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         e = cudaMalloc(&c->f[k], pop);
         if (e == cudaSuccess && params->thermal) e = cudaMalloc(&c->g[k], pop);
-        if (e == cudaSuccess && dev16(c)) e = cudaMalloc(&c->R[k], 2 * (size_t)(D + 3) * (size_t)N);
+        if (e == cudaSuccess && dev16(c)) e = cudaMalloc(&c->R[k], evlbm::kRecBytes * (size_t)N);
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->red, evlbm::totals_work_bytes(N));
     if (e == cudaSuccess) e = cudaMalloc(&c->RT_iso, c->real_bytes * (size_t)N);
@@ -274,7 +274,8 @@ int lbm_step(lbm_ctx *c, int n_steps)
             e = evlbm::fused2d_step(c->P.precision, c->K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx], c->RT_iso,
                                     c->stream);
         else if (fused3)
-            e = evlbm::fused3d_step(c->K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx], c->RT_iso, c->stream);
+            e = evlbm::fused3d_step(c->P.precision, c->K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx], c->RT_iso,
+                                    c->R[c->cur], c->R[nx], c->stream);
         else if (fp64(c))
             e = evlbm::ref_step_f64(c->Q, c->K, c->scratch, c->RT_iso, c->f[c->cur], c->g[c->cur], c->f[nx],
                                     c->g[nx], c->stream);
@@ -388,7 +389,34 @@ int lbm_launches_per_step(const lbm_ctx *c)
     return (!fp64(c) && (evlbm::fused2d_supported(c->P.precision, c->Q, c->K) ||
                          evlbm::fused3d_supported(c->P.precision, c->Q, c->K)))
                ? 1
-               : 4;
+               : (c->K.walls ? 5 : 4);
+}
+
+int lbm_set_walls(lbm_ctx *c, int enable, const double u_lo[3], const double u_hi[3], double T_w)
+{
+    if (!c) return LBM_EINVAL;
+    if (enable != 0 && enable != 1) return fail(c, LBM_EINVAL, "enable must be 0 or 1");
+    if (!enable) {
+        c->K.walls = 0;
+        return LBM_OK;
+    }
+    if (!u_lo || !u_hi) return fail(c, LBM_EINVAL, "u_lo and u_hi must be 3-vectors");
+    if (dev16(c)) return fail(c, LBM_EINVAL, "walls need FP64 or FP32 storage");
+    if (c->P.nx < 3) return fail(c, LBM_EINVAL, "walls need nx >= 3");
+    if (c->P.kappa != 0.0) return fail(c, LBM_EINVAL, "walls need kappa = 0 (a single-phase fluid)");
+    if (!(T_w > 0.0) || !isfinite(T_w)) return fail(c, LBM_EINVAL, "T_w must be finite and > 0");
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(u_lo[a]) || !isfinite(u_hi[a])) return fail(c, LBM_EINVAL, "wall velocities must be finite");
+        if (a == 0 && (u_lo[a] != 0.0 || u_hi[a] != 0.0))
+            return fail(c, LBM_EINVAL, "the walls move parallel to themselves (u_x = 0)");
+        if (a == 2 && c->D == 2 && (u_lo[a] != 0.0 || u_hi[a] != 0.0))
+            return fail(c, LBM_EINVAL, "D2Q9: u_z of the walls must be 0");
+        c->K.wall_u[0][a] = u_lo[a];
+        c->K.wall_u[1][a] = u_hi[a];
+    }
+    c->K.wall_RT = c->P.R * T_w;
+    c->K.walls = 1;
+    return LBM_OK;
 }
 
 int lbm_set_tile(lbm_ctx *c, int tile_w, int tile_h)
@@ -439,7 +467,8 @@ static int autotune3d(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
         for (int s = 0; s <= probe_steps && e == cudaSuccess; ++s) {
             if (s == 1) e = cudaEventRecord(e0, c->stream);
             if (e == cudaSuccess)
-                e = evlbm::fused3d_step(K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx], c->RT_iso, c->stream);
+                e = evlbm::fused3d_step(c->P.precision, K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx],
+                                        c->RT_iso, c->R[c->cur], c->R[nx], c->stream);
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -597,7 +626,7 @@ int lbm_interface(int eos, double a, double b, double RT, double kappa, double o
 namespace {
 
 constexpr char kCkMagic[8] = {'E', 'V', 'L', 'B', 'M', 'C', 'K', 'P'};
-constexpr uint32_t kCkVersion = 1;
+constexpr uint32_t kCkVersion = 2;            // 2: 16-bit storage records are FP32, 24 bytes per node
 constexpr size_t kCkHeader = 8 + 4 + 4 + 8 * 4 + 6 * 8 + 8 + 4 * 8;
 constexpr size_t kCkChunk = 64u << 20;          // host staging per transfer
 
@@ -615,7 +644,7 @@ CkLayout ck_layout(const lbm_ctx *c)
     L.dev[1] = c->g[c->cur];
     L.bytes[1] = c->P.thermal ? pop : 0;
     L.dev[2] = c->R[c->cur];
-    L.bytes[2] = dev16(c) ? 2 * (size_t)(c->D + 3) * (size_t)c->N : 0;
+    L.bytes[2] = dev16(c) ? evlbm::kRecBytes * (size_t)c->N : 0;
     L.dev[3] = c->RT_iso;
     L.bytes[3] = c->P.thermal ? 0 : c->real_bytes * (size_t)c->N;
     return L;

@@ -133,6 +133,8 @@ __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_batch(Bat
         A.lambda = B.lambda;
         A.c_eq = B.c_eq;
         A.c_star = B.c_star;
+        A.walls = 0;
+        A.wall_uy[0] = A.wall_uy[1] = A.wall_RT = 0.f;
         const int y0 = (k / D.strips) * D.H;
         fused_tile<kW, THERMAL, true>(A, k % D.strips, y0, min(D.H, D.ny - y0), 0, smem);
         __syncthreads();

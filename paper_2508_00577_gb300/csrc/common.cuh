@@ -20,7 +20,19 @@ struct KParams {
     double c_eq;         // 2 beta
     double c_star;       // (dt/lambda)(1 - beta)
     int tile_w, tile_h;  // launch shape of the fused kernel (0 = default)
+    int walls;           // 1: the columns x = 0 and x = nx-1 are wall nodes (lbm_set_walls)
+    double wall_u[2][3]; // velocity of the wall at x = 0 and at x = nx-1
+    double wall_RT;      // R T_w of both walls
 };
+
+// Wall nodes (the thermal Couette set-up: u and T prescribed at x = 0 and x = L_x; the
+// paper gives no wall scheme, the reading here is a diffusely reflecting wall): with walls
+// on, the columns x = 0 and x = nx-1 do not stream (their moments are those of their own
+// populations), carry no force and do not collide; they absorb the populations streaming
+// into them (mass m) and their populations become the equilibria f^eq(rho_w, u_w,
+// theta0(rho_w, R T_w)), g^eq(rho_w, u_w, R T_w) (Eqs. feq, geq) with P_E(rho_w, R T_w) = 2 m,
+// which returns the absorbed mass to the fluid.
+__host__ __device__ inline bool wall_col(const KParams &p, int x) { return p.walls && (x == 0 || x == p.nx - 1); }
 
 // Velocity set: i = (cx+1) + 3(cy+1) + 9(cz+1).
 __host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include "common.cuh"
+#include "dev16.cuh"
 
 namespace evlbm {
 
@@ -19,7 +20,7 @@ cudaError_t expand_f64(int Q, const KParams &p, const void *src, double *dst, in
 
 // Stage kernels in FP32; storage 1 = FP32, 2 = FP16, 3 = BF16.  16-bit storage holds
 // deviations from each node's own local equilibrium plus that node's reference
-// state R ([D + 3][N] in the same format, double-buffered: Rin read, Rout written).
+// record R ([N] of kRecBytes, dev16.cuh; double-buffered: Rin read, Rout written).
 cudaError_t ref_init_f32(int prec, int Q, const KParams &p, const void *rho, const void *u, const void *RT, void *f,
                          void *g, void *Rout, cudaStream_t st);
 cudaError_t ref_macro_f32(int prec, int Q, const KParams &p, void *scratch, const void *RT_iso, const void *f,
@@ -31,11 +32,12 @@ cudaError_t ref_export_f32(int Q, const KParams &p, void *scratch, double R, flo
 cudaError_t expand_f32(int prec, int Q, const KParams &p, const void *src, const void *R, double *dst, int which,
                        cudaStream_t st);
 
-// Scratch layout of the stage kernels: rho, j, Gam, Pi, lap, A, F, u, RT, theta0, P0, gamma0, flux, wq.
-constexpr int kRefFieldCount = 30;
+// Scratch layout of the stage kernels: rho, j, Gam, Pi, lap, A, F, u, RT, theta0, P0, gamma0, flux, wq,
+// m_in (mass streaming into each wall node).
+constexpr int kRefFieldCount = 31;
 struct FieldOffsets {
     static constexpr long long rho = 0, j = 1, Gam = 4, Pi = 5, lap = 14, A = 15, F = 16, u = 19, RT = 22,
-                               theta0 = 23, P0 = 24, gamma0 = 25, flux = 26, wq = 29;
+                               theta0 = 23, P0 = 24, gamma0 = 25, flux = 26, wq = 29, m_in = 30;
 };
 
 // Fused single-pass D2Q9 step (FP32 arithmetic); prec 1/2/3 as above.  The
@@ -47,12 +49,13 @@ constexpr int kTileBalanced = -1;
 extern const int kFusedWidths[kFusedWidthCount];
 void fused2d_default_tile(const KParams &p, int *W, int *H);
 bool fused2d_supported(int prec, int Q, const KParams &p);
-// Fused single-pass D3Q27 step (FP32, divergence force form); the x-y tile is
+// Fused single-pass D3Q27 step (FP32 arithmetic, divergence force form; storage prec
+// 1/2/3 as above, 16-bit storage reading Rin and writing Rout); the x-y tile is
 // kFused3dTile x kFused3dTile columns, tile_h is the z-chunk height (0 = default).
 constexpr int kFused3dTile = 16;
 bool fused3d_supported(int prec, int Q, const KParams &p);
-cudaError_t fused3d_step(const KParams &p, const void *f, const void *g, void *fo, void *go, const void *RT_iso,
-                         cudaStream_t st);
+cudaError_t fused3d_step(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
+                         const void *RT_iso, const void *Rin, void *Rout, cudaStream_t st);
 cudaError_t fused2d_step(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
                          const void *RT_iso, cudaStream_t st);
 

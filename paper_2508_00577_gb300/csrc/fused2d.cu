@@ -8,12 +8,12 @@ namespace {
 
 using namespace fused;
 
-template <int kW, bool THERMAL>
+template <int kW, bool THERMAL, bool WALLS>
 __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_fused2d(FusedArgs A)
 {
     extern __shared__ v2 smem[];
     const int y0 = blockIdx.y * A.H;                       // H is even
-    fused_tile<kW, THERMAL, false>(A, blockIdx.x, y0, min(A.H, A.ny - y0), blockIdx.z, smem);
+    fused_tile<kW, THERMAL, false, WALLS>(A, blockIdx.x, y0, min(A.H, A.ny - y0), blockIdx.z, smem);
 }
 
 // Balanced persistent variant: a grid of S x parts CTAs (S strips, parts = the
@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_fused2d(F
 // then march over the same rows at the same time, as in the chunked grid, so the
 // halo columns they share are re-read from L2 and each row is fetched from DRAM in
 // one stretch.  A share that crosses the end of a layer becomes two tiles.
-template <int kW, bool THERMAL>
+template <int kW, bool THERMAL, bool WALLS>
 __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_fused2d_bal(FusedArgs A)
 {
     extern __shared__ v2 smem[];
@@ -35,28 +35,28 @@ __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_fused2d_b
         const int p0 = (int)(g - (long long)layer * P);
         const int p1 = (int)min((long long)P, p0 + (g1 - g));
         const int y0 = 2 * p0;
-        fused_tile<kW, THERMAL, false>(A, strip, y0, min(2 * p1, A.ny) - y0, layer, smem);
+        fused_tile<kW, THERMAL, false, WALLS>(A, strip, y0, min(2 * p1, A.ny) - y0, layer, smem);
         __syncthreads();
         g += p1 - p0;
     }
 }
 
-template <int W, bool THERMAL>
+template <int W, bool THERMAL, bool WALLS>
 cudaError_t launch_w(const FusedArgs &A, int nz, bool balanced, cudaStream_t st)
 {
     static bool attr = false;
     static int resident = 0;
     constexpr size_t smem = smem_of<W>();
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused2d<W, THERMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_fused2d<W, THERMAL, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fused2d_bal<W, THERMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_fused2d_bal<W, THERMAL, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
         int per_sm = 0, dev = 0, sms = 0;
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused2d_bal<W, THERMAL>, threads_of<W>(),
-                                                              smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused2d_bal<W, THERMAL, WALLS>,
+                                                              threads_of<W>(), smem);
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
@@ -67,22 +67,22 @@ cudaError_t launch_w(const FusedArgs &A, int nz, bool balanced, cudaStream_t st)
     if (balanced) {
         const int S = (A.nx + W - 1) / W;
         const long long parts = min((long long)max(resident / S, 1), (long long)nz * ((A.ny + 1) / 2));
-        k_fused2d_bal<W, THERMAL><<<(unsigned)(S * parts), threads_of<W>(), smem, st>>>(A);
+        k_fused2d_bal<W, THERMAL, WALLS><<<(unsigned)(S * parts), threads_of<W>(), smem, st>>>(A);
     } else {
         const dim3 grid((A.nx + W - 1) / W, (A.ny + A.H - 1) / A.H, nz);
-        k_fused2d<W, THERMAL><<<grid, threads_of<W>(), smem, st>>>(A);
+        k_fused2d<W, THERMAL, WALLS><<<grid, threads_of<W>(), smem, st>>>(A);
     }
     return cudaGetLastError();
 }
 
-template <bool THERMAL>
+template <bool THERMAL, bool WALLS>
 cudaError_t launch(int W, const FusedArgs &A, int nz, bool balanced, cudaStream_t st)
 {
     switch (W) {
-    case 64: return launch_w<64, THERMAL>(A, nz, balanced, st);
-    case 96: return launch_w<96, THERMAL>(A, nz, balanced, st);
-    case 192: return launch_w<192, THERMAL>(A, nz, balanced, st);
-    default: return launch_w<128, THERMAL>(A, nz, balanced, st);
+    case 64: return launch_w<64, THERMAL, WALLS>(A, nz, balanced, st);
+    case 96: return launch_w<96, THERMAL, WALLS>(A, nz, balanced, st);
+    case 192: return launch_w<192, THERMAL, WALLS>(A, nz, balanced, st);
+    default: return launch_w<128, THERMAL, WALLS>(A, nz, balanced, st);
     }
 }
 
@@ -125,11 +125,17 @@ cudaError_t fused2d_step(int prec, const KParams &p, const void *f, const void *
     A.lambda = float(p.lambda);
     A.c_eq = float(p.c_eq);
     A.c_star = float(p.c_star);
+    A.walls = p.walls;
+    A.wall_uy[0] = float(p.wall_u[0][1]);
+    A.wall_uy[1] = float(p.wall_u[1][1]);
+    A.wall_RT = float(p.wall_RT);
     int W = p.tile_w, H = p.tile_h;
     const bool balanced = W > 0 && H == kTileBalanced;
     if (W <= 0 || (H <= 0 && !balanced)) fused2d_default_tile(p, &W, &H);
     A.H = balanced ? 0 : H + (H & 1);  // row pairs: chunks of an even number of rows
-    return p.thermal ? launch<true>(W, A, p.nz, balanced, st) : launch<false>(W, A, p.nz, balanced, st);
+    if (p.walls)
+        return p.thermal ? launch<true, true>(W, A, p.nz, balanced, st) : launch<false, true>(W, A, p.nz, balanced, st);
+    return p.thermal ? launch<true, false>(W, A, p.nz, balanced, st) : launch<false, false>(W, A, p.nz, balanced, st);
 }
 
 }  // namespace evlbm

@@ -89,6 +89,8 @@ struct FusedArgs {
     unsigned N;                  // nodes of the lattice (Q*N < 2^31)
     int eos;
     float a, b, kappa, lambda, c_eq, c_star;
+    int walls;                   // 1: the columns x = 0 and x = nx-1 are wall nodes (KParams::walls)
+    float wall_uy[2], wall_RT;   // wall velocities (along y) and R T_w
 };
 
 __device__ __forceinline__ int wrap_any(int v, int n)
@@ -121,6 +123,19 @@ __device__ __forceinline__ void pull18(const float *__restrict__ base, unsigned 
     }
 }
 
+// A wall column's own populations of rows (r, r+1): wall nodes do not stream.
+template <bool CG>
+__device__ __forceinline__ void pull_own(const float *__restrict__ base, unsigned N, const unsigned ro[4], int col,
+                                         v2 h[9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float *p = base + i * N + col;
+        const float *p0 = p + ro[1], *p1 = p + ro[2];
+        h[i] = V(in_bounds(p0 - base, 9ull * N) ? ldpop<CG>(p0) : 0.f, in_bounds(p1 - base, 9ull * N) ? ldpop<CG>(p1) : 0.f);
+    }
+}
+
 __device__ __forceinline__ v2 sum9(const v2 h[9])
 {
     return ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
@@ -129,8 +144,9 @@ __device__ __forceinline__ v2 sum9(const v2 h[9])
 // One tile: rows y0 .. y0 + rows - 1 (y0 even, y0 + rows <= ny) of strip bx of layer
 // bz.  smem holds smem_of<kW>() bytes.  CG selects loads that may see populations
 // written by other CTAs of the same launch.  A CTA that runs several tiles must pass a
-// barrier between them (the rings are reused).
-template <int kW, bool THERMAL, bool CG>
+// barrier between them (the rings are reused).  WALLS compiles in the wall columns
+// (FusedArgs::walls); without it the kernel has no trace of them.
+template <int kW, bool THERMAL, bool CG, bool WALLS = false>
 __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, int rows, int bz, v2 *smem)
 {
     constexpr int S = slots_of<kW>();
@@ -174,6 +190,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
     int cols[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) cols[k] = wrap_any(col - 1 + k, nx);
+    // Wall column (x = 0 or nx-1 with walls on): no streaming, no force, no collision.
+    const bool wallc = WALLS && A.walls && (cols[1] == 0 || cols[1] == nx - 1);
     // Shared rings: stages B and C read slot +- 1, stage D the thread-private rings at t.
     // A thread that fails the check does no work but still reaches every barrier.
     if (!in_bounds(slot, S) || ((inB || inC) && !(in_bounds(slot - 1, S) && in_bounds(slot + 1, S))) ||
@@ -182,6 +200,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
 
     const float a = A.a, b = A.b, kappa = A.kappa, lambda = A.lambda;
     const unsigned N = A.N;
+    auto pull = [&](const float *base, const unsigned ro[4], v2 h[9]) {
+        if (wallc) pull_own<CG>(base, N, ro, cols[1], h);
+        else pull18<CG>(base, N, ro, cols, h);
+    };
     auto rows4 = [&](int r, unsigned ro[4]) {      // rows r-1 .. r+2 of the layer
         const int rp = next_row(r, ny);
         ro[0] = layer + (unsigned)prev_row(r, ny) * nx;
@@ -203,12 +225,12 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
     if (inA) {
         unsigned ro[4];
         rows4(rA, ro);
-        pull18<CG>(A.f, N, ro, cols, pf);
+        pull(A.f, ro, pf);
     }
     if (THERMAL && inC) {
         unsigned ro[4];
         rows4(rC, ro);
-        pull18<CG>(A.g, N, ro, cols, pg);
+        pull(A.g, ro, pg);
     }
 
     for (int q = qbeg; q <= qend; ++q) {
@@ -221,14 +243,32 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
             fld(JY, s0)[slot] = ((pf[6] + pf[7]) + pf[8]) - ((pf[0] + pf[1]) + pf[2]);
             if (inD) {
                 v2 *fr = f9 + (q & 3) * 9 * kW + t;
+                if (WALLS && wallc) {
+                    // A wall column keeps, for stage D, the mass streaming into it: the three
+                    // populations moving toward it, pulled from the fluid column next to it.
+                    unsigned ro[4];
+                    rows4(rA, ro);
+                    const int s = cols[1] == 0 ? -1 : 1;
+                    v2 m = V(0.f);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) fr[i * kW] = pf[i];
+                    for (int cy = -1; cy <= 1; ++cy) {
+                        const int i = (s + 1) + 3 * (cy + 1);
+                        const float *pp = A.f + i * N + cols[1 - s];
+                        const float *p0 = pp + ro[1 - cy], *p1 = pp + ro[2 - cy];
+                        m = m + V(in_bounds(p0 - A.f, 9ull * N) ? ldpop<CG>(p0) : 0.f,
+                                  in_bounds(p1 - A.f, 9ull * N) ? ldpop<CG>(p1) : 0.f);
+                    }
+                    fr[0] = m;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) fr[i * kW] = pf[i];
+                }
             }
             rA = next_row(next_row(rA, ny), ny);
             if (q < qend) {
                 unsigned ro[4];
                 rows4(rA, ro);
-                pull18<CG>(A.f, N, ro, cols, pf);
+                pull(A.f, ro, pf);
             }
         }
         __syncthreads();
@@ -276,7 +316,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
             const v2 dyPyy = fma2(V(1.f / 3.f), north(z2, z1, slot) - south(z3, z2, slot),
                                   V(1.f / 12.f) * ((north(z2, z1, se) + north(z2, z1, sw)) -
                                                    (south(z3, z2, se) + south(z3, z2, sw))));
-            const v2 Fx = -(dxPxx + dyPxy), Fy = -(dxPxy + dyPyy);
+            const v2 Fx = wallc ? V(0.f) : -(dxPxx + dyPxy), Fy = wallc ? V(0.f) : -(dxPxy + dyPyy);
             const v2 rho = fld(RHO, sm2)[slot];
             const v2 ir = rcp2(rho);
             const v2 ux = fma2(V(0.5f), Fx, fld(JX, sm2)[slot]) * ir;
@@ -295,7 +335,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
                 if (q + 1 <= qend) {           // prefetch the next stage-C pair
                     unsigned ro[4];
                     rows4(rC, ro);
-                    pull18<CG>(A.g, N, ro, cols, pg);
+                    pull(A.g, ro, pg);
                 }
             } else {
                 const float *Tp = A.RT_iso + layer + cols[1];
@@ -337,7 +377,65 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
         __syncthreads();
 
         // ---------------- D: collide pair q-3 ----------------
-        if (inD && q - 3 >= q0) {
+        if (inD && q - 3 >= q0 && wallc) {
+            // Wall nodes (diffuse reflection): the equilibria at the wall velocity (0, U_w) and
+            // temperature R T_w (Eqs. feq, geq) with the density rho_w that returns the mass m
+            // that streamed in, P_E(rho_w, R T_w) = 2 m.
+            const int p = q - 3;
+            const v2 P = V(2.f) * f9[(p & 3) * 9 * kW + t];
+            const float U = cols[1] == 0 ? A.wall_uy[0] : A.wall_uy[1], RTw = A.wall_RT;
+            v2 rho, Z;
+            if (A.eos == 0) {
+                rho = P * rcp2(fma2(V(b), P, V(RTw)));             // P / (RT + b P)
+                Z = rcp2(V(1.f) - V(b) * rho);
+            } else {
+                // Newton on rho RT Z(eta) = P, dP_E/drho = RT (1 + 4 eta + 4 eta^2 - 4 eta^3 + eta^4)/(1 - eta)^4
+                rho = P * V(1.f / RTw);
+                for (int k = 0; k < 16; ++k) {
+                    const v2 eta = V(0.25f * b) * rho;
+                    const v2 num = fma2(eta, fma2(eta, V(1.f) - eta, V(1.f)), V(1.f));
+                    const v2 iom = rcp2(V(1.f) - eta);
+                    const v2 z = num * (iom * iom) * iom;
+                    const v2 dn = fma2(eta, fma2(eta, fma2(eta, eta - V(4.f), V(4.f)), V(4.f)), V(1.f));
+                    rho = rho - (fma2(rho * V(RTw), z, -P)) * rcp2(V(RTw) * dn * ((iom * iom) * (iom * iom)));
+                }
+                const v2 eta = V(0.25f * b) * rho;
+                const v2 num = fma2(eta, fma2(eta, V(1.f) - eta, V(1.f)), V(1.f));
+                const v2 iom = rcp2(V(1.f) - eta);
+                Z = num * (iom * iom) * iom;
+            }
+            const v2 th = V(RTw) * Z;
+            const v2 hr = V(0.5f) * rho;
+            const v2 zey = th + V(U * U);
+            const v2 ex[3] = {hr * th, rho - rho * th, hr * th};
+            const v2 ey[3] = {V(0.5f) * (zey - V(U)), V(1.f) - zey, V(0.5f) * (zey + V(U))};
+            const unsigned out0 = layer + (unsigned)rD * nx + cols[1];
+            const unsigned out1 = layer + (unsigned)next_row(rD, ny) * nx + cols[1];
+            const bool second = 2 * p + 1 < y0 + Heff;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const v2 o = ex[i % 3] * ey[i / 3];
+                if (in_bounds(i * N + out0, 9ull * N)) A.fo[i * N + out0] = o.x;
+                if (second && in_bounds(i * N + out1, 9ull * N)) A.fo[i * N + out1] = o.y;
+            }
+            if constexpr (THERMAL) {
+                // g^eq = rho [(e P_x + S_x) P_y + P_x S_y], u_x = 0: S_x = (th^2/2, -th^2, th^2/2).
+                const float e = 1.5f * RTw;
+                const v2 th2 = th * th;
+                const v2 Sx[3] = {V(0.5f) * th2, -th2, V(0.5f) * th2};
+                const float S0 = 0.5f * U * U;
+                const v2 S1 = V(U) * (th + V(S0)), S2 = fma2(th, th, V(U * U) * fma2(V(2.5f), th, V(S0)));
+                const v2 Sy[3] = {V(0.5f) * (S2 - S1), V(S0) - S2, V(0.5f) * (S2 + S1)};
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int ix = i % 3, iy = i / 3;
+                    const v2 o = fma2(fma2(V(e), ex[ix], rho * Sx[ix]), ey[iy], ex[ix] * Sy[iy]);
+                    if (in_bounds(i * N + out0, 9ull * N)) A.go[i * N + out0] = o.x;
+                    if (second && in_bounds(i * N + out1, 9ull * N)) A.go[i * N + out1] = o.y;
+                }
+            }
+            rD = next_row(next_row(rD, ny), ny);
+        } else if (inD && q - 3 >= q0) {
             const int p = q - 3;                   // its stage C ran at iteration q-1
             const v2 rho = cprev[0], Fx = cprev[1], Fy = cprev[2], RT = cprev[3], th = cprev[4], g0 = cprev[5];
             const int sw = slot - 1, se = slot + 1;

@@ -1,6 +1,7 @@
 // Fused single-pass D3Q27 step of the Enskog-Vlasov lattice Boltzmann model
-// (Karlin & Hosseini, arXiv 2508.00577), FP32 storage and arithmetic: one
-// launch per time step does pull streaming, raw moments, the Enskog-gauge force
+// (Karlin & Hosseini, arXiv 2508.00577), FP32 arithmetic with FP32 or 16-bit
+// (FP16 / BF16 deviation, dev16.cuh) population storage: one launch per time
+// step does pull streaming, raw moments, the Enskog-gauge force
 // in divergence (Korteweg-stress) form, the shifted velocity and energy
 // (Eqs. u_shift, T_shift), the EOS and gamma0 (Eq. gamma), the corrections
 // Phi, Phi', q' (Eqs. correction_u/gamma/q), the equilibria (Eqs. feq, f_star,
@@ -20,7 +21,13 @@
 // centre values pass from C to D through a one-plane per-thread slot (stage C takes
 // the tile column a thread collides in D first, and reads the slot before rewriting
 // it); at 80.7 KB per CTA two CTAs leave the L1 ~92 KB for loads in flight.
+//
+// 16-bit storage: every pulled population is rebuilt from its source node's
+// reference record (one 16-byte load per pulled population, L1/L2 hits after the
+// first) and the stored deviation; stage D writes the node's new record and the
+// deviations of its populations from the record's equilibria.
 #include "bounds.cuh"
+#include "dev16.cuh"
 #include "dispatch.h"
 
 namespace evlbm {
@@ -41,9 +48,11 @@ constexpr int O_CEN = O_CF + 21 * SC;             // [7][NT]  rho Fx Fy Fz RT th
 constexpr int SMEM_FLOATS = O_CEN + 7 * NT;
 constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
 
-struct Args {
-    const float *f, *g;
-    float *fo, *go;
+template <typename S> struct Args {
+    const S *f, *g;
+    S *fo, *go;
+    const float *Rin;                             // reference records read (16-bit storage)
+    float *Rout;                                  // reference records written
     const float *RT_iso;
     int nx, ny, nz, HZ;
     unsigned N;
@@ -61,15 +70,31 @@ __device__ __forceinline__ float rcpa(float a)
 }
 
 // Global loads and stores with the bounds check of checked builds (no-op otherwise).
+// 16-bit storage loads and stores the raw deviation.
 __device__ __forceinline__ float ldc(const float *base, unsigned off, unsigned long long n)
 {
     return in_bounds(off, n) ? __ldg(base + off) : 0.f;
+}
+template <typename S>
+__device__ __forceinline__ float ldc(const S *base, unsigned off, unsigned long long n)
+{
+    return in_bounds(off, n) ? Bits16<S>::to_f(__ldg(reinterpret_cast<const unsigned short *>(base) + off)) : 0.f;
 }
 __device__ __forceinline__ void stc(float *base, unsigned off, unsigned long long n, float v)
 {
     if (in_bounds(off, n)) __stcs(base + off, v);
 }
-
+template <typename S>
+__device__ __forceinline__ void stc(S *base, unsigned off, unsigned long long n, float v)
+{
+    if (in_bounds(off, n)) __stcs(reinterpret_cast<unsigned short *>(base) + off, Bits16<S>::from_f(v));
+}
+// Reference record of node n (16-bit storage).
+__device__ __forceinline__ Ref16 ldrec(const float *R, unsigned n, unsigned long long N)
+{
+    if (!in_bounds(n, N)) return Ref16{1.f, {0.f, 0.f, 0.f}, 0.f, 0.f};
+    return load_rec(R, (long long)N, n);
+}
 __device__ __forceinline__ int wrapi(int v, int n)
 {
     v %= n;
@@ -128,9 +153,13 @@ __device__ __forceinline__ void psi3_poly(float A0, float A1, float A2, float ou
     out[2] = 0.5f * (A2 + A1);
 }
 
-template <bool THERMAL>
-__global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
+// Two resident CTAs per SM (128 registers per thread).  The thermal kernel with 16-bit
+// storage spills ~190 B per thread at that budget; one CTA per SM with 245 registers and
+// no spill was measured slower (2.11 against 2.49 GLUPS at 256^3).
+template <bool THERMAL, typename S>
+__global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
 {
+    constexpr bool DEV = Store<S>::dev;
     extern __shared__ float sm[];
     const int t = threadIdx.x;
     const int nx = A.nx, ny = A.ny, nz = A.nz;
@@ -179,7 +208,9 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                 float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
                 for (int i = 0; i < 27; ++i) {
-                    const float h = ldc(A.f, src_of(i, c, zo, N), 27ull * N);
+                    const unsigned si = src_of(i, c, zo, N);
+                    float h = ldc(A.f, si, 27ull * N);
+                    if constexpr (DEV) h = decode_f<27>(cxi(i), cyi(i), czi(i), ldrec(A.Rin, si - i * N, N), h);
                     rho += h;
                     if (cxi(i) == 1) jx += h; else if (cxi(i) == -1) jx -= h;
                     if (cyi(i) == 1) jy += h; else if (cyi(i) == -1) jy -= h;
@@ -296,7 +327,12 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
                     const Cell c = cell_of(x0 + cx, y0 + cy, nx, ny);
                     float Gam = 0.f;
 #pragma unroll
-                    for (int i = 0; i < 27; ++i) Gam += ldc(A.g, src_of(i, c, zo, N), 27ull * N);
+                    for (int i = 0; i < 27; ++i) {
+                        const unsigned si = src_of(i, c, zo, N);
+                        float h = ldc(A.g, si, 27ull * N);
+                        if constexpr (DEV) h = decode_g<27>(cxi(i), cyi(i), czi(i), ldrec(A.Rin, si - i * N, N), h);
+                        Gam += h;
+                    }
                     const float E = (Gam + 0.5f * (ux * Fx + uy * Fy + uz * Fz)) * ir;
                     RT = (2.f / 3.f) * (E - 0.5f * (ux * ux + uy * uy + uz * uz));
                 } else {
@@ -367,129 +403,180 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args A)
             const float usx = ux + Fx * lir, usy = uy + Fy * lir, usz = uz + Fz * lir;
             // Separable equilibria: h_i = X[c_ix] * YZ[c_iy][c_iz] (+ X'[c_ix] * YZ'[..]),
             // the per-axis Psi factors combined once per node (Eqs. feq, f_star, geq, gstar).
+            // f^eq and g^eq are evaluated with the rounding-exact functions of the 16-bit
+            // storage references (dev16.cuh): there they are the references themselves.
             float ex[3], ey[3], ez[3], sx[3], sy[3], sz[3];
-            psi3(ux, th + ux * ux, ex);
-            psi3(uy, th + uy * uy, ey);
-            psi3(uz, th + uz * uz, ez);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                ex[k] = refP(k - 1, ux, th);
+                ey[k] = refP(k - 1, uy, th);
+                ez[k] = refP(k - 1, uz, th);
+            }
             psi3(usx, th + usx * usx + Phx * lir, sx);
             psi3(usy, th + usy * usy + Phy * lir, sy);
             psi3(usz, th + usz * usz + Phz * lir, sz);
-            float rex[3], rsx[3], Eyz[9], Syz[9];
+            float rex[3], rsx[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                rex[k] = rho * ex[k];
+                rex[k] = __fmul_rn(rho, ex[k]);
                 rsx[k] = rho * sx[k];
             }
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    Eyz[3 * j + k] = ey[j] * ez[k];
-                    Syz[3 * j + k] = sy[j] * sz[k];
-                }
 
             unsigned zo[3];
             plane_offsets(p, nx, ny, nz, zo);
             const unsigned out = (unsigned)wrapi(p, nz) * (unsigned)nx * (unsigned)ny +
                                  (unsigned)(y0 + dcy) * (unsigned)nx + (unsigned)(x0 + dcx);
             const float kh = 1.f - A.c_eq, keq = A.c_eq - A.c_star, kst = A.c_star;
-#pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                const int ix = cxi(i) + 1, iyz = 3 * (cyi(i) + 1) + czi(i) + 1;
-                // The output is not read again this step: a streaming store keeps L2 for
-                // the populations the stages still share.
-                const float h = ldc(A.f, src_of(i, cD, zo, N), 27ull * N);
-                stc(A.fo, (unsigned)i * N + out, 27ull * N, kh * h + keq * (rex[ix] * Eyz[iyz]) + kst * (rsx[ix] * Syz[iyz]));
+            const float e = __fmul_rn(1.5f, RT);
+            // 16-bit storage: this node's new reference record (rho, u, theta0, e); the
+            // deviations written are taken against the equilibria computed here from it.
+            float inv_f = 0.f, inv_g = 0.f;
+            if constexpr (DEV) {
+                if (in_bounds(out, N)) {
+                    __stcs(reinterpret_cast<float4 *>(A.Rout) + out, make_float4(rho, ux, uy, uz));
+                    __stcs(reinterpret_cast<float2 *>(A.Rout + 4ull * N) + out, make_float2(th, e));
+                }
+                inv_f = rcpa(rho);
+                inv_g = THERMAL ? rcpa(rho * e) : 0.f;
             }
+            // g^eq_i = rho [e PP_x PP_y PP_z + PS_x PP_y PP_z + PP_x PS_y PP_z + PP_x PP_y PS_z]
+            //        = rho (e PP_x + PS_x) [PP_y PP_z] + rho PP_x [PS_y PP_z + PP_y PS_z],
+            // e = 3/2 RT, PP = Psi(u, theta0 + u^2), PS = Psi applied to (u^2/2,
+            // theta0 u + u^3/2, theta0^2 + 5/2 theta0 u^2 + u^4/2); g* the same at
+            // (u*, RT*) without Phi, plus g' = 1/2 c_i . q' on the |c| = 1 populations.
+            float Ag[3], As[3], rpx[3], Sy[3], Sz[3], Ty[3], Tz[3], py[3], pz[3];
+            float hq[3] = {0.f, 0.f, 0.f};
             if (THERMAL) {
-                // g^eq_i = rho [e PP_x PP_y PP_z + PS_x PP_y PP_z + PP_x PS_y PP_z + PP_x PP_y PS_z]
-                //        = rho (e PP_x + PS_x) [PP_y PP_z] + rho PP_x [PS_y PP_z + PP_y PS_z],
-                // e = 3/2 RT, PP = Psi(u, theta0 + u^2), PS = Psi applied to (u^2/2,
-                // theta0 u + u^3/2, theta0^2 + 5/2 theta0 u^2 + u^4/2); g* the same at
-                // (u*, RT*) without Phi, plus g' = 1/2 c_i . q' on the |c| = 1 populations.
-                const float e = 1.5f * RT;
                 const float es = e - 0.5f * (Fx * Fx + Fy * Fy + Fz * Fz) * (lir * lir);
                 auto psiS = [&](float v, float o3[3]) {
                     const float vv = v * v;
                     psi3_poly(0.5f * vv, v * (th + 0.5f * vv), th * th + vv * (2.5f * th + 0.5f * vv), o3);
                 };
-                float S[3], T[3], px[3], py[3], pz[3];
-                float Ag[3], As[3], rpx[3], Cyz[9], Pyz[9], Dyz[9];
-                psiS(ux, S);
+                float T[3], px[3];
                 psi3(usx, th + usx * usx, px);
                 psiS(usx, T);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    Ag[k] = rho * (e * ex[k] + S[k]);
+                    Ag[k] = ref_A(rho, e, ex[k], refS(k - 1, ux, th));
                     rpx[k] = rho * px[k];
                     As[k] = rho * (es * px[k] + T[k]);
+                    Sy[k] = refS(k - 1, uy, th);
+                    Sz[k] = refS(k - 1, uz, th);
                 }
-                float Sy[3], Sz[3], Ty[3], Tz[3];
-                psiS(uy, Sy);
-                psiS(uz, Sz);
                 psiS(usy, Ty);
                 psiS(usz, Tz);
                 psi3(usy, th + usy * usy, py);
                 psi3(usz, th + usz * usz, pz);
+                hq[0] = 0.5f * qx;
+                hq[1] = 0.5f * qy;
+                hq[2] = 0.5f * qz;
+            }
+            auto sel3 = [](const float v[3], int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); };
+            // One c_z layer of nine populations per pass; with 16-bit storage the passes are
+            // not unrolled, which bounds how many source records the compiler keeps in flight.
+#pragma unroll(DEV ? 1 : 3)
+            for (int kz = 0; kz < 3; ++kz) {
+                const int cz = kz - 1;
+                const float ezk = sel3(ez, kz), szk = sel3(sz, kz);
+                const unsigned zs = cz == 1 ? zo[0] : (cz == 0 ? zo[1] : zo[2]);     // plane of z - c_z
+                float E[3], Sl[3];
 #pragma unroll
-                for (int j = 0; j < 3; ++j)
+                for (int j = 0; j < 3; ++j) {
+                    E[j] = __fmul_rn(ey[j], ezk);
+                    Sl[j] = sy[j] * szk;
+                }
+                const float iwz = cz ? 6.f : 1.5f;
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        Cyz[3 * j + k] = Sy[j] * ez[k] + ey[j] * Sz[k];
-                        Pyz[3 * j + k] = py[j] * pz[k];
-                        Dyz[3 * j + k] = Ty[j] * pz[k] + py[j] * Tz[k];
+                for (int j = 0; j < 9; ++j) {
+                    const int cx = j % 3 - 1, cy = j / 3 - 1;
+                    const unsigned sn = zs + cD.yo[1 - cy] + cD.xo[1 - cx];       // source node
+                    const unsigned i = (unsigned)j + 9u * (unsigned)kz;
+                    // The output is not read again this step: a streaming store keeps L2 for
+                    // the populations the stages still share.
+                    float h = ldc(A.f, i * N + sn, 27ull * N);
+                    if constexpr (DEV) {
+                        const Ref16 r = ldrec(A.Rin, sn, N);
+                        const float rPx = __fmul_rn(r.rho, refP(cx, r.u[0], r.th));
+                        const float PyPz = __fmul_rn(refP(cy, r.u[1], r.th), refP(cz, r.u[2], r.th));
+                        const float w = cz ? wgt16<27>(cx, cy, 1) : wgt16<27>(cx, cy, 0);
+                        h = __fmaf_rn(__fmul_rn(w, r.rho), h, ref_f_of(rPx, PyPz));
                     }
-                const float hq[3] = {0.5f * qx, 0.5f * qy, 0.5f * qz};
+                    const float feq = ref_f_of(rex[cx + 1], E[cy + 1]);
+                    float v = kh * h + keq * feq + kst * (rsx[cx + 1] * Sl[cy + 1]);
+                    if constexpr (DEV)
+                        v = (v - feq) * (inv_f * ((cx ? 6.f : 1.5f) * (cy ? 6.f : 1.5f) * iwz));
+                    stc(A.fo, i * N + out, 27ull * N, v);
+                }
+                if (THERMAL) {
+                    const float Szk = sel3(Sz, kz), pzk = sel3(pz, kz), Tzk = sel3(Tz, kz);
+                    float C[3], P[3], Dd[3];
 #pragma unroll
-                for (int i = 0; i < 27; ++i) {
-                    const int ix = cxi(i) + 1, iyz = 3 * (cyi(i) + 1) + czi(i) + 1;
-                    const float h = ldc(A.g, src_of(i, cD, zo, N), 27ull * N);
-                    const float geq = Ag[ix] * Eyz[iyz] + rex[ix] * Cyz[iyz];
-                    float gst = As[ix] * Pyz[iyz] + rpx[ix] * Dyz[iyz];
-                    if (abs(cxi(i)) + abs(cyi(i)) + abs(czi(i)) == 1)
-                        gst += (cxi(i) ? cxi(i) * hq[0] : 0.f) + (cyi(i) ? cyi(i) * hq[1] : 0.f) +
-                               (czi(i) ? czi(i) * hq[2] : 0.f);
-                    stc(A.go, (unsigned)i * N + out, 27ull * N, kh * h + keq * geq + kst * gst);
+                    for (int j = 0; j < 3; ++j) {
+                        C[j] = ref_D(ey[j], Sy[j], ezk, Szk);
+                        P[j] = py[j] * pzk;
+                        Dd[j] = Ty[j] * pzk + py[j] * Tzk;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 9; ++j) {
+                        const int cx = j % 3 - 1, cy = j / 3 - 1;
+                        const unsigned sn = zs + cD.yo[1 - cy] + cD.xo[1 - cx];
+                        const unsigned i = (unsigned)j + 9u * (unsigned)kz;
+                        float h = ldc(A.g, i * N + sn, 27ull * N);
+                        if constexpr (DEV) {
+                            const Ref16 r = ldrec(A.Rin, sn, N);
+                            const float Px = refP(cx, r.u[0], r.th), Py = refP(cy, r.u[1], r.th);
+                            const float Pz = refP(cz, r.u[2], r.th);
+                            const float ref = ref_g_of(ref_A(r.rho, r.e, Px, refS(cx, r.u[0], r.th)),
+                                                       __fmul_rn(r.rho, Px), __fmul_rn(Py, Pz),
+                                                       ref_D(Py, refS(cy, r.u[1], r.th), Pz, refS(cz, r.u[2], r.th)));
+                            const float w = cz ? wgt16<27>(cx, cy, 1) : wgt16<27>(cx, cy, 0);
+                            h = __fmaf_rn(__fmul_rn(__fmul_rn(w, r.rho), r.e), h, ref);
+                        }
+                        const float geq = ref_g_of(Ag[cx + 1], rex[cx + 1], E[cy + 1], C[cy + 1]);
+                        float gst = As[cx + 1] * P[cy + 1] + rpx[cx + 1] * Dd[cy + 1];
+                        // g' on the |c| = 1 populations
+                        if (cx != 0 && cy == 0) gst += cz == 0 ? cx * hq[0] : 0.f;
+                        if (cx == 0 && cy != 0) gst += cz == 0 ? cy * hq[1] : 0.f;
+                        if (cx == 0 && cy == 0) gst += float(cz) * hq[2];
+                        float v = kh * h + keq * geq + kst * gst;
+                        if constexpr (DEV)
+                            v = (v - geq) * (inv_g * ((cx ? 6.f : 1.5f) * (cy ? 6.f : 1.5f) * iwz));
+                        stc(A.go, i * N + out, 27ull * N, v);
+                    }
                 }
             }
         }
     }
 }
 
-template <bool THERMAL>
-cudaError_t launch(const Args &A, cudaStream_t st)
+template <bool THERMAL, typename S>
+cudaError_t launch(const Args<S> &A, cudaStream_t st)
 {
     static int attr_dev = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (attr_dev != dev) {
-        e = cudaFuncSetAttribute(k_fused3d<THERMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        e = cudaFuncSetAttribute(k_fused3d<THERMAL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
     const dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY, (A.nz + A.HZ - 1) / A.HZ);
-    k_fused3d<THERMAL><<<grid, NT, SMEM_BYTES, st>>>(A);
+    k_fused3d<THERMAL, S><<<grid, NT, SMEM_BYTES, st>>>(A);
     return cudaGetLastError();
 }
 
-}  // namespace
-
-EVLBM_DEFINE_OOB_READER(fused3d_oob)
-
-bool fused3d_supported(int prec, int Q, const KParams &p)
+template <typename S>
+cudaError_t step_t(const KParams &p, const void *f, const void *g, void *fo, void *go, const void *RT_iso,
+                   const void *Rin, void *Rout, cudaStream_t st)
 {
-    return prec == 1 && Q == 27 && p.force_form == 0 && (long long)27 * p.N < (1LL << 31);
-}
-
-cudaError_t fused3d_step(const KParams &p, const void *f, const void *g, void *fo, void *go, const void *RT_iso,
-                         cudaStream_t st)
-{
-    Args A;
-    A.f = static_cast<const float *>(f);
-    A.g = static_cast<const float *>(g);
-    A.fo = static_cast<float *>(fo);
-    A.go = static_cast<float *>(go);
+    Args<S> A;
+    A.f = static_cast<const S *>(f);
+    A.g = static_cast<const S *>(g);
+    A.fo = static_cast<S *>(fo);
+    A.go = static_cast<S *>(go);
+    A.Rin = static_cast<const float *>(Rin);
+    A.Rout = static_cast<float *>(Rout);
     A.RT_iso = static_cast<const float *>(RT_iso);
     A.nx = p.nx;
     A.ny = p.ny;
@@ -503,7 +590,24 @@ cudaError_t fused3d_step(const KParams &p, const void *f, const void *g, void *f
     A.c_eq = float(p.c_eq);
     A.c_star = float(p.c_star);
     A.HZ = p.tile_h > 0 ? p.tile_h : (p.nz < 64 ? p.nz : 64);
-    return p.thermal ? launch<true>(A, st) : launch<false>(A, st);
+    return p.thermal ? launch<true, S>(A, st) : launch<false, S>(A, st);
+}
+
+}  // namespace
+
+EVLBM_DEFINE_OOB_READER(fused3d_oob)
+
+bool fused3d_supported(int prec, int Q, const KParams &p)
+{
+    return prec >= 1 && prec <= 3 && Q == 27 && p.force_form == 0 && !p.walls && (long long)27 * p.N < (1LL << 31);
+}
+
+cudaError_t fused3d_step(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
+                         const void *RT_iso, const void *Rin, void *Rout, cudaStream_t st)
+{
+    if (prec == 2) return step_t<__half>(p, f, g, fo, go, RT_iso, Rin, Rout, st);
+    if (prec == 3) return step_t<__nv_bfloat16>(p, f, g, fo, go, RT_iso, Rin, Rout, st);
+    return step_t<float>(p, f, g, fo, go, RT_iso, Rin, Rout, st);
 }
 
 }  // namespace evlbm

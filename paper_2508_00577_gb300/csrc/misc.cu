@@ -15,7 +15,7 @@ constexpr int kRedThreads = 256;
 // in a fixed tree; the result does not depend on scheduling.  16-bit storage is
 // expanded with the node's reference equilibrium first.
 template <typename S, int Q>
-__global__ void __launch_bounds__(kRedThreads) k_totals_partial(KParams p, const S *f, const S *g, const S *R,
+__global__ void __launch_bounds__(kRedThreads) k_totals_partial(KParams p, const S *f, const S *g, const float *R,
                                                                  double *partial, int *nonfinite)
 {
     __shared__ double sh[5][kRedThreads];
@@ -24,12 +24,12 @@ __global__ void __launch_bounds__(kRedThreads) k_totals_partial(KParams p, const
     const long long N = p.N;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
-        RefState<float> r{};
-        if constexpr (Store<S>::dev) r = load_ref<float, S, Q>(R, N, n);
+        Ref16 r{};
+        if constexpr (Store<S>::dev) r = load_rec(R, N, n);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             double fi = double(Store<S>::load(f + i * N + n));
-            if constexpr (Store<S>::dev) fi = double(ref_f<float, Q>(i, r) + fscale<float, Q>(i, r) * float(fi));
+            if constexpr (Store<S>::dev) fi = double(decode_f<Q>(cx_of(i), cy_of(i), cz_of(i, Q), r, float(fi)));
             bad |= !isfinite(fi);
             acc[0] += fi;
             const int c[3] = {cx_of(i), cy_of(i), cz_of(i, Q)};
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kRedThreads) k_totals_partial(KParams p, const
                 acc[1 + a] += c[a] == 1 ? fi : (c[a] == -1 ? -fi : 0.0);
             if (p.thermal) {
                 double gi = double(Store<S>::load(g + i * N + n));
-                if constexpr (Store<S>::dev) gi = double(ref_g<float, Q>(i, r) + gscale<float, Q>(i, r) * float(gi));
+                if constexpr (Store<S>::dev) gi = double(decode_g<Q>(cx_of(i), cy_of(i), cz_of(i, Q), r, float(gi)));
                 bad |= !isfinite(gi);
                 acc[4] += gi;
             }
@@ -88,10 +88,10 @@ cudaError_t totals_s(int Q, const KParams &p, const void *f, const void *g, cons
     if (e != cudaSuccess) return e;
     if (Q == 9)
         k_totals_partial<S, 9><<<kRedBlocks, kRedThreads, 0, st>>>(
-            p, static_cast<const S *>(f), static_cast<const S *>(g), static_cast<const S *>(R), partial, flag);
+            p, static_cast<const S *>(f), static_cast<const S *>(g), static_cast<const float *>(R), partial, flag);
     else
         k_totals_partial<S, 27><<<kRedBlocks, kRedThreads, 0, st>>>(
-            p, static_cast<const S *>(f), static_cast<const S *>(g), static_cast<const S *>(R), partial, flag);
+            p, static_cast<const S *>(f), static_cast<const S *>(g), static_cast<const float *>(R), partial, flag);
     k_totals_final<<<1, 1024, 0, st>>>(partial, out);
     return cudaGetLastError();
 }

@@ -20,8 +20,8 @@
 
 namespace {
 
-// Largest lattice (nodes) the static scratch holds: 30 FP64 fields per node,
-// 32768 nodes -> 7.5 MiB of device memory per GPU that loads the library.
+// Largest lattice (nodes) the static scratch holds: 31 FP64 fields per node,
+// 32768 nodes -> 7.75 MiB of device memory per GPU that loads the library.
 constexpr long long kNoallocMaxNodes = 32768;
 
 static __device__ __align__(256) double g_noalloc_scratch[evlbm::kRefFieldCount * kNoallocMaxNodes];

@@ -12,6 +12,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dev16.cuh"
 
 namespace evlbm {
 
@@ -24,61 +25,10 @@ __host__ __device__ constexpr int c_of(int i, int a, int Q)
     return a == 0 ? cx_of(i) : (a == 1 ? cy_of(i) : cz_of(i, Q));
 }
 
-// ---------------------------------------------------------------------------
-// 16-bit storage.  A node stores its populations as deviations from its own
-// local equilibrium, delta_i(x) = h~_i(x) - h^eq_i(R(x)), next to the reference
-// R(x) = (rho, u, theta0, RT) of that node in the same 16-bit format.  The
-// reference is rounded to 16 bits before it is used on either side, so a puller
-// reconstructs exactly the value the writer meant: h_i(y) = h^eq_i(R(y - c_i)) +
-// delta_i(y - c_i).  FP32/FP64 storage holds the populations themselves.
-// ---------------------------------------------------------------------------
-template <typename real> struct RefState {
-    real rho, u[3], th, RT;
-};
-
-template <typename S> __device__ __forceinline__ float ld16(const S *p) { return Store<S>::load(p); }
-
-// R layout: [D + 3][N] = rho, u_x, u_y, (u_z), theta0, RT.
-template <typename real, typename S, int Q>
-__device__ __forceinline__ RefState<real> load_ref(const S *R, long long N, long long n)
-{
-    constexpr int D = (Q == 9) ? 2 : 3;
-    RefState<real> r;
-    r.rho = real(ld16<S>(R + n));
-    r.u[0] = r.u[1] = r.u[2] = real(0);
-#pragma unroll
-    for (int a = 0; a < D; ++a) r.u[a] = real(ld16<S>(R + (1 + a) * N + n));
-    r.th = real(ld16<S>(R + (1 + D) * N + n));
-    r.RT = real(ld16<S>(R + (2 + D) * N + n));
-    return r;
-}
-
-// Rounds a state to the 16-bit format (what load_ref will return after store_ref).
-template <typename real, typename S, int Q>
-__device__ __forceinline__ RefState<real> round_ref(real rho, const real *u, real th, real RT)
-{
-    constexpr int D = (Q == 9) ? 2 : 3;
-    auto r16 = [](real v) { return real(Store<S>::round(float(v))); };
-    RefState<real> r;
-    r.rho = r16(rho);
-    r.u[0] = r.u[1] = r.u[2] = real(0);
-#pragma unroll
-    for (int a = 0; a < D; ++a) r.u[a] = r16(u[a]);
-    r.th = r16(th);
-    r.RT = r16(RT);
-    return r;
-}
-
-template <typename real, typename S, int Q>
-__device__ __forceinline__ void store_ref(S *R, long long N, long long n, const RefState<real> &r)
-{
-    constexpr int D = (Q == 9) ? 2 : 3;
-    Store<S>::store(R + n, float(r.rho));
-#pragma unroll
-    for (int a = 0; a < D; ++a) Store<S>::store(R + (1 + a) * N + n, float(r.u[a]));
-    Store<S>::store(R + (1 + D) * N + n, float(r.th));
-    Store<S>::store(R + (2 + D) * N + n, float(r.RT));
-}
+// 16-bit storage (dev16.cuh): a node stores its populations as deviations from its
+// own local equilibrium next to its 16-byte reference record; a puller rebuilds
+// h_i(y) = h^eq_i(R(y - c_i)) + w_i rho_R delta_i(y - c_i) (times e_R for g).
+// FP32/FP64 storage holds the populations themselves.
 
 struct Node {
     int x, y, z;
@@ -221,43 +171,6 @@ __device__ __forceinline__ real geq_i(int i, real rho, const real *u, real theta
     return rho * (e * pP + sS);
 }
 
-// Scales of the stored deviations: w_i rho_r for f, w_i rho_r (3/2 RT_r) for g.  They
-// keep the stored numbers near 1e-3..1, inside FP16's normal range.
-template <typename real, int Q>
-__device__ __forceinline__ real fscale(int i, const RefState<real> &r) { return real(w_of(i, Q)) * r.rho; }
-template <typename real, int Q>
-__device__ __forceinline__ real gscale(int i, const RefState<real> &r)
-{
-    return real(w_of(i, Q)) * r.rho * (real(1.5) * r.RT);
-}
-
-// 1 / w_i = prod_a (3/2 or 6): the weights are prod_a (2/3 or 1/6), so the reciprocal is
-// a product of exact binary factors.
-template <typename real, int Q>
-__device__ __forceinline__ real inv_w(int i)
-{
-    real r = real(1.0);
-#pragma unroll
-    for (int a = 0; a < Lat<Q>::D; ++a) r = r * (c_of(i, a, Q) == 0 ? real(1.5) : real(6.0));
-    return r;
-}
-
-// Equilibria of a reference state (population i).
-template <typename real, int Q>
-__device__ __forceinline__ real ref_f(int i, const RefState<real> &r)
-{
-    real z[3] = {0, 0, 0};
-#pragma unroll
-    for (int a = 0; a < Lat<Q>::D; ++a) z[a] = r.th + r.u[a] * r.u[a];
-    return prod_eq<real, Q>(i, r.rho, r.u, z);
-}
-
-template <typename real, int Q>
-__device__ __forceinline__ real ref_g(int i, const RefState<real> &r)
-{
-    return geq_i<real, Q>(i, r.rho, r.u, r.th, r.RT);
-}
-
 // ---------------------------------------------------------------------------
 // Scratch fields of the stage kernels (each [N] unless noted).
 // ---------------------------------------------------------------------------
@@ -265,12 +178,13 @@ template <typename real> struct RefFields {
     real *rho, *j /*[3][N]*/, *Gam;
     real *Pi /*[9][N]*/, *lap, *A;
     real *F /*[3][N]*/, *u /*[3][N]*/, *RT, *theta0, *P0, *gamma0, *flux /*[3][N]*/, *wq;
+    real *m_in;           // mass streaming into each wall node this step (walls on)
     const real *RT_iso;   // frozen R*T field (thermal = 0)
 };
 
 // Initial populations f = f^eq(rho, u, theta0(rho, RT)), g = g^eq(rho, u, RT).
 template <typename real, typename S, int Q>
-__global__ void k_init(KParams p, const real *rho_in, const real *u_in, const real *RT_in, S *f, S *g, S *Rout)
+__global__ void k_init(KParams p, const real *rho_in, const real *u_in, const real *RT_in, S *f, S *g, float *Rout)
 {
     Node nd;
     if (!node_of(p, nd)) return;
@@ -286,16 +200,17 @@ __global__ void k_init(KParams p, const real *rho_in, const real *u_in, const re
         u[a] = u_in[a * N + n];
         zeta[a] = theta0 + u[a] * u[a];
     }
-    RefState<real> ref{};
+    EncTab tab{};
     if constexpr (Store<S>::dev) {
-        ref = round_ref<real, S, Q>(rho, u, theta0, RT);
-        store_ref<real, S, Q>(Rout, N, n, ref);
+        const Ref16 r = make_rec(float(rho), float(u[0]), float(u[1]), float(u[2]), float(theta0), float(RT));
+        store_rec(Rout, N, n, r);
+        enc_tab<Q>(r, p.thermal != 0, tab);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const real v = prod_eq<real, Q>(i, rho, u, zeta);
         if constexpr (Store<S>::dev)
-            Store<S>::store(f + i * N + n, float((v - ref_f<real, Q>(i, ref)) / fscale<real, Q>(i, ref)));
+            Store<S>::store(f + i * N + n, encode_f<Q>(cx_of(i), cy_of(i), cz_of(i, Q), tab, float(v)));
         else Store<S>::store(f + i * N + n, v);
     }
     if (p.thermal) {
@@ -303,7 +218,7 @@ __global__ void k_init(KParams p, const real *rho_in, const real *u_in, const re
         for (int i = 0; i < Q; ++i) {
             const real v = geq_i<real, Q>(i, rho, u, theta0, RT);
             if constexpr (Store<S>::dev)
-                Store<S>::store(g + i * N + n, float((v - ref_g<real, Q>(i, ref)) / gscale<real, Q>(i, ref)));
+                Store<S>::store(g + i * N + n, encode_g<Q>(cx_of(i), cy_of(i), cz_of(i, Q), tab, float(v)));
             else Store<S>::store(g + i * N + n, v);
         }
     }
@@ -311,18 +226,19 @@ __global__ void k_init(KParams p, const real *rho_in, const real *u_in, const re
 
 // Pulled populations h_i(x) = h~_i(x - c_i) of one node, f and (thermal) g.
 template <typename real, typename S, int Q>
-__device__ __forceinline__ void pull_node(const KParams &p, const Node &nd, const S *f, const S *g, const S *Rin,
+__device__ __forceinline__ void pull_node(const KParams &p, const Node &nd, const S *f, const S *g, const float *Rin,
                                           real *fo, real *go)
 {
     const long long N = p.N;
+    const bool wall = wall_col(p, nd.x);                 // a wall node keeps its own populations
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const long long src = shifted(p, nd, -cx_of(i), -cy_of(i), -cz_of(i, Q));
+        const long long src = wall ? nd.n : shifted(p, nd, -cx_of(i), -cy_of(i), -cz_of(i, Q));
         if constexpr (Store<S>::dev) {
-            const RefState<real> r = load_ref<real, S, Q>(Rin, N, src);
-            fo[i] = ref_f<real, Q>(i, r) + fscale<real, Q>(i, r) * real(Store<S>::load(f + i * N + src));
+            const Ref16 r = load_rec(Rin, N, src);
+            fo[i] = decode_f<Q>(cx_of(i), cy_of(i), cz_of(i, Q), r, Store<S>::load(f + i * N + src));
             if (p.thermal)
-                go[i] = ref_g<real, Q>(i, r) + gscale<real, Q>(i, r) * real(Store<S>::load(g + i * N + src));
+                go[i] = decode_g<Q>(cx_of(i), cy_of(i), cz_of(i, Q), r, Store<S>::load(g + i * N + src));
         } else {
             fo[i] = real(Store<S>::load(f + i * N + src));
             if (p.thermal) go[i] = real(Store<S>::load(g + i * N + src));
@@ -333,7 +249,7 @@ __device__ __forceinline__ void pull_node(const KParams &p, const Node &nd, cons
 // Stages 1-2: pull streaming f_i(x) = f~_i(x - c_i) and the raw moments
 // rho = sum f_i, j_a = sum c_ia f_i, Gamma = sum g_i (ascending i).
 template <typename real, typename S, int Q>
-__global__ void k_moments(KParams p, const S *f, const S *g, const S *Rin, RefFields<real> w)
+__global__ void k_moments(KParams p, const S *f, const S *g, const float *Rin, RefFields<real> w)
 {
     Node nd;
     if (!node_of(p, nd)) return;
@@ -358,6 +274,16 @@ __global__ void k_moments(KParams p, const S *f, const S *g, const S *Rin, RefFi
 #pragma unroll
     for (int a = 0; a < D; ++a) w.j[a * N + n] = j[a];
     w.Gam[n] = Gam;
+    if (wall_col(p, nd.x)) {
+        // Mass streaming into this wall node: the populations moving toward it (c_x = -1 at
+        // x = 0, +1 at x = nx-1) pulled from the fluid, in ascending i.
+        const int s = nd.x == 0 ? -1 : 1;
+        real m = real(0.0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (cx_of(i) == s) m = m + real(Store<S>::load(f + i * N + shifted(p, nd, -cx_of(i), -cy_of(i), -cz_of(i, Q))));
+        w.m_in[n] = m;
+    }
 }
 
 // Stage 3a: the Korteweg stress (divergence form) or the literal-form inputs.
@@ -415,6 +341,7 @@ __global__ void k_macro(KParams p, RefFields<real> w)
         } else {
             F[d] = grad_iso<real, Q>(p, nd, w.A, d) + real(p.kappa) * rho * grad_iso<real, Q>(p, nd, w.lap, d);
         }
+        if (wall_col(p, nd.x)) F[d] = real(0.0);           // no force on wall nodes
         u[d] = (w.j[d * N + n] + real(0.5) * F[d]) / rho;
     }
     real RT;
@@ -452,10 +379,11 @@ __global__ void k_macro(KParams p, RefFields<real> w)
 // collision h~ = h + 2 beta (h^eq - h) + (dt/lambda)(1 - beta)(h* - h^eq).
 template <typename real, typename S, int Q>
 __global__ void k_collide(KParams p, RefFields<real> w, const S *f_src, const S *g_src, S *f_dst, S *g_dst,
-                          const S *Rin, S *Rout)
+                          const float *Rin, float *Rout)
 {
     Node nd;
     if (!node_of(p, nd)) return;
+    if (wall_col(p, nd.x)) return;                       // wall nodes: k_walls
     constexpr int D = Lat<Q>::D;
     const long long N = p.N, n = nd.n;
     const real lambda = real(p.lambda), c_eq = real(p.c_eq), c_star = real(p.c_star);
@@ -487,15 +415,11 @@ __global__ void k_collide(KParams p, RefFields<real> w, const S *f_src, const S 
     }
     real fs[Q], gs[Q];
     pull_node<real, S, Q>(p, nd, f_src, g_src, Rin, fs, gs);
-    RefState<real> ref{};
-    // 16-bit storage: the deviations are scaled by 1 / (w_i rho_r) and 1 / (w_i rho_r 3/2 RT_r)
-    // as products with the per-node reciprocals and the exact 1/w_i, not as 2Q divisions.
-    real inv_fs = real(0.0), inv_gs = real(0.0);
+    EncTab tab{};
     if constexpr (Store<S>::dev) {
-        ref = round_ref<real, S, Q>(rho, u, theta0, RT);
-        store_ref<real, S, Q>(Rout, N, n, ref);
-        inv_fs = real(1.0) / ref.rho;
-        inv_gs = real(1.0) / (ref.rho * (real(1.5) * ref.RT));
+        const Ref16 r = make_rec(float(rho), float(u[0]), float(u[1]), float(u[2]), float(theta0), float(RT));
+        store_rec(Rout, N, n, r);
+        enc_tab<Q>(r, p.thermal != 0, tab);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -504,8 +428,7 @@ __global__ void k_collide(KParams p, RefFields<real> w, const S *f_src, const S 
         const real fst = prod_eq<real, Q>(i, rho, us, zs);
         const real v = h + c_eq * (feq - h) + c_star * (fst - feq);
         if constexpr (Store<S>::dev)
-            Store<S>::store(f_dst + i * N + n,
-                            float((v - ref_f<real, Q>(i, ref)) * (inv_fs * inv_w<real, Q>(i))));
+            Store<S>::store(f_dst + i * N + n, encode_f<Q>(cx_of(i), cy_of(i), cz_of(i, Q), tab, float(v)));
         else Store<S>::store(f_dst + i * N + n, v);
     }
     if (p.thermal) {
@@ -531,11 +454,62 @@ __global__ void k_collide(KParams p, RefFields<real> w, const S *f_src, const S 
             }
             const real v = h + c_eq * (geq - h) + c_star * (gst - geq);
             if constexpr (Store<S>::dev)
-                Store<S>::store(g_dst + i * N + n,
-                                float((v - ref_g<real, Q>(i, ref)) * (inv_gs * inv_w<real, Q>(i))));
+                Store<S>::store(g_dst + i * N + n, encode_g<Q>(cx_of(i), cy_of(i), cz_of(i, Q), tab, float(v)));
             else Store<S>::store(g_dst + i * N + n, v);
         }
     }
+}
+
+// Density rho_w of a wall node at temperature RT with P_E(rho_w, RT) = P: van der Waals
+// form in closed form, rho = P / (RT + b P); Carnahan-Starling by sixteen Newton steps from
+// the ideal-gas value P / RT, dP_E/drho = RT (1 + 4 eta + 4 eta^2 - 4 eta^3 + eta^4)/(1 - eta)^4.
+template <typename real>
+__device__ __forceinline__ real wall_density(const KParams &p, real P, real RT)
+{
+    const real b = real(p.b);
+    if (p.eos == 0) return P / (RT + b * P);
+    real rho = P / RT;
+    for (int k = 0; k < 16; ++k) {
+        const real eta = b * rho / real(4.0);
+        const real num = real(1.0) + eta + eta * eta - eta * eta * eta;
+        const real om = real(1.0) - eta;
+        const real Z = num / (om * om * om);
+        const real dn = real(1.0) + real(4.0) * eta + real(4.0) * eta * eta - real(4.0) * eta * eta * eta +
+                        eta * eta * eta * eta;
+        rho = rho - (rho * RT * Z - P) / (RT * (dn / (om * om * om * om)));
+    }
+    return rho;
+}
+
+// Wall nodes after the collision (diffuse reflection): the equilibria at the wall velocity
+// and temperature with the density rho_w that returns the absorbed mass m_in, P_E(rho_w) =
+// 2 m_in (the populations leaving a wall with u_x = 0 carry rho_w theta0 / 2).  One thread
+// per wall node: index k < 2 ny nz, side k % 2 (0: x = 0, 1: x = nx-1).  FP32/FP64 storage.
+template <typename real, typename S, int Q>
+__global__ void k_walls(KParams p, RefFields<real> w, S *f, S *g)
+{
+    constexpr int D = Lat<Q>::D;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2LL * p.ny * p.nz) return;
+    const int side = (int)(k % 2);
+    const long long row = k / 2;                          // y + ny z
+    const long long N = p.N, n = row * p.nx + (side ? p.nx - 1 : 0);
+    const real RT = real(p.wall_RT);
+    const real rho = wall_density<real>(p, real(2.0) * w.m_in[n], RT);
+    real Z, g0;
+    eos_Zg<real>(p.eos, p.thermal, real(p.b), rho, Z, g0);
+    const real theta0 = RT * Z;
+    real u[3] = {0, 0, 0}, zeta[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        u[a] = real(p.wall_u[side][a]);
+        zeta[a] = theta0 + u[a] * u[a];
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Store<S>::store(f + i * N + n, prod_eq<real, Q>(i, rho, u, zeta));
+    if (p.thermal)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Store<S>::store(g + i * N + n, geq_i<real, Q>(i, rho, u, theta0, RT));
 }
 
 // Output of the macroscopic fields as FP32 (device) for callers that keep them on the GPU.
@@ -556,19 +530,19 @@ __global__ void k_export_f32(KParams p, RefFields<real> w, double R, float *rho,
 // Post-collision populations expanded to FP64 (16-bit storage adds the node's
 // reference equilibrium back).
 template <typename S, int Q>
-__global__ void k_expand(KParams p, const S *src, const S *R, double *dst, int which)
+__global__ void k_expand(KParams p, const S *src, const float *R, double *dst, int which)
 {
     Node nd;
     if (!node_of(p, nd)) return;
     const long long N = p.N, n = nd.n;
-    RefState<float> r{};
-    if constexpr (Store<S>::dev) r = load_ref<float, S, Q>(R, N, n);
+    Ref16 r{};
+    if constexpr (Store<S>::dev) r = load_rec(R, N, n);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         double v = double(Store<S>::load(src + i * N + n));
         if constexpr (Store<S>::dev)
-            v = which == 0 ? double(ref_f<float, Q>(i, r) + fscale<float, Q>(i, r) * float(v))
-                           : double(ref_g<float, Q>(i, r) + gscale<float, Q>(i, r) * float(v));
+            v = which == 0 ? double(decode_f<Q>(cx_of(i), cy_of(i), cz_of(i, Q), r, float(v)))
+                           : double(decode_g<Q>(cx_of(i), cy_of(i), cz_of(i, Q), r, float(v)));
         dst[i * N + n] = v;
     }
 }

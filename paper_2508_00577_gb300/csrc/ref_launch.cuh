@@ -26,6 +26,7 @@ inline RefFields<real> ref_fields(void *scratch, long long N, const void *RT_iso
     w.gamma0 = b;       b += N;
     w.flux = b;         b += 3 * N;
     w.wq = b;           b += N;
+    w.m_in = b;         b += N;
     w.RT_iso = static_cast<const real *>(RT_iso);
     return w;
 }
@@ -40,7 +41,7 @@ cudaError_t ref_init_t(const KParams &p, const void *rho, const void *u, const v
     k_init<real, S, Q><<<node_grid(p.N, B), B, 0, st>>>(p, static_cast<const real *>(rho),
                                                         static_cast<const real *>(u),
                                                         static_cast<const real *>(RT), static_cast<S *>(f),
-                                                        static_cast<S *>(g), static_cast<S *>(Rout));
+                                                        static_cast<S *>(g), static_cast<float *>(Rout));
     return cudaGetLastError();
 }
 
@@ -52,7 +53,7 @@ cudaError_t ref_macro_t(const KParams &p, void *scratch, const void *RT_iso, con
     const dim3 G = node_grid(p.N, B);
     RefFields<real> w = ref_fields<real>(scratch, p.N, RT_iso);
     k_moments<real, S, Q><<<G, B, 0, st>>>(p, static_cast<const S *>(f), static_cast<const S *>(g),
-                                           static_cast<const S *>(Rin), w);
+                                           static_cast<const float *>(Rin), w);
     k_stress<real, Q><<<G, B, 0, st>>>(p, w);
     k_macro<real, Q><<<G, B, 0, st>>>(p, w);
     return cudaGetLastError();
@@ -68,8 +69,15 @@ cudaError_t ref_step_t(const KParams &p, void *scratch, const void *RT_iso, cons
     RefFields<real> w = ref_fields<real>(scratch, p.N, RT_iso);
     k_collide<real, S, Q><<<node_grid(p.N, B), B, 0, st>>>(p, w, static_cast<const S *>(f),
                                                            static_cast<const S *>(g), static_cast<S *>(fo),
-                                                           static_cast<S *>(go), static_cast<const S *>(Rin),
-                                                           static_cast<S *>(Rout));
+                                                           static_cast<S *>(go), static_cast<const float *>(Rin),
+                                                           static_cast<float *>(Rout));
+    if constexpr (!Store<S>::dev) {
+        if (p.walls) {
+            const long long nw = 2LL * p.ny * p.nz;
+            k_walls<real, S, Q><<<(unsigned)((nw + B - 1) / B), B, 0, st>>>(p, w, static_cast<S *>(fo),
+                                                                             static_cast<S *>(go));
+        }
+    }
     return cudaGetLastError();
 }
 
@@ -86,7 +94,7 @@ template <typename S, int Q>
 cudaError_t expand_t(const KParams &p, const void *src, const void *R, double *dst, int which, cudaStream_t st)
 {
     const int B = 256;
-    k_expand<S, Q><<<node_grid(p.N, B), B, 0, st>>>(p, static_cast<const S *>(src), static_cast<const S *>(R), dst,
+    k_expand<S, Q><<<node_grid(p.N, B), B, 0, st>>>(p, static_cast<const S *>(src), static_cast<const float *>(R), dst,
                                                     which);
     return cudaGetLastError();
 }
