@@ -31,6 +31,11 @@ NX = NY = 1024
 TRS = (0.7, 0.8, 0.9)
 RADII = (64.0, 128.0, 256.0)
 A, B, KAPPA, TAU = 0.1, 4.0, 0.116, 0.3
+# The ensemble's capillarity: kappa = 0.2 (10-90 % width 5.3 at T/Tc = 0.7, 9.6 at 0.9), as
+# the surrogate workload; at 0.116 26 of the 512 domains diverge within 5000 steps, at 0.2 nine
+# (coalescing pairs at T/Tc ~ 0.70, which the FP64 oracle does not hold either).
+ENSEMBLE_KAPPA = 0.2
+ENSEMBLE_STEPS = 5000
 BYTES_PER_LU = 2 * 9 * 2 * 4          # D2Q9, f and g, read + write, FP32
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch on this workload, per launch
 # shape (W, H) of the fused kernel (H = -1: the balanced grid, k_fused2d_bal), from one ncu
@@ -343,13 +348,17 @@ def run(args):
         # The other rows, measured on their own workloads: the batched persistent
         # ensemble (A11) and the 3-D path with reduced-precision storage (A10).
         eargs = argparse.Namespace(**vars(args))
-        eargs.domains, eargs.steps, eargs.warmup, eargs.tile = 512, 2000, 20, ""
+        eargs.domains, eargs.steps, eargs.warmup, eargs.tile = 512, ENSEMBLE_STEPS, 20, ""
         e_line = run_ensemble(eargs)
         line["ensemble"] = {k: e_line[k] for k in ("metric", "value", "unit", "steps", "ms_per_step", "config",
                                                      "roofline", "finite", "finite_domains")}
         sargs3 = argparse.Namespace(**vars(args))
         sargs3.steps, sargs3.warmup, sargs3.tile = 20, 3, ""
         line["spinodal3d"] = run_spinodal3d(sargs3)
+        # Physics checks of the same kernels (not timed): the Laplace law of droplets and
+        # the paper's supersonic thermal Couette flow.
+        line["laplace"] = {k: v for k, v in run_laplace(args).items() if k not in ("data",)}
+        line["couette"] = {k: v for k, v in run_couette(args).items() if k not in ("data",)}
     if world == 1 and not args.no_surrogate:
         # The learned-surrogate row: speedup of surrogate + fallback over the plain
         # LB at <= 1e-2 relative density error (separate workload, see run_surrogate).
@@ -381,7 +390,8 @@ def run_ensemble(args):
         rv, rl = cache[tr]
         r, v, t = inputs.two_droplets(dm["nx"], dm["ny"], dm["r1"], dm["r2"], dm["gap"], rv, rl, dm["tr"] * Tc)
         rho.append(r); u.append(v); T.append(t); sizes.append((dm["nx"], dm["ny"]))
-    params = ev.lbm_params.make(eos=ev.LBM_EOS_CS, a=A, b=B, kappa=KAPPA, tau=TAU, thermal=1, precision=ev.LBM_FP32)
+    params = ev.lbm_params.make(eos=ev.LBM_EOS_CS, a=A, b=B, kappa=ENSEMBLE_KAPPA, tau=TAU, thermal=1,
+                                precision=ev.LBM_FP32)
     stream = torch.cuda.Stream()
     bt = ev.Batch(params, sizes, rho, u, T, stream=stream.cuda_stream)
     if args.tile:                       # fixed W,H launch shape (the one a profile captures)
@@ -412,7 +422,7 @@ def run_ensemble(args):
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"ensemble: {len(sizes)} uneven D2Q9 thermal domains (64..512)^2, FP32, "
-                               "one persistent launch per call under a CUDA graph",
+                               f"kappa {ENSEMBLE_KAPPA}, {args.steps} steps in one persistent launch under a CUDA graph",
                    "nodes": N, "tile": {"w": tile[0], "h": tile[1], "autotuned": not args.tile}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (ENSEMBLE_TRAFFIC_BYTES_PER_STEP[tuple(tile)] / 1e9
@@ -606,7 +616,8 @@ def run_spinodal3d(args):
     the spinodal region at T/Tc = 0.85 with seeded uniform +-1 % noise, u = 0; FP32
     storage and arithmetic, and FP16 / BF16 deviation storage with FP32 arithmetic.
     One line with MLUPS and the fraction of the HBM roofline per storage type
-    (algorithmic bytes: 2 populations x 27 x read + write x storage bytes)."""
+    (algorithmic bytes: 2 populations x 27 x read + write x storage bytes, plus for
+    16-bit storage the 24-byte FP32 reference record of every node, read and written)."""
     import torch
 
     import paper_2508_00577_gb300 as ev
@@ -625,11 +636,11 @@ def run_spinodal3d(args):
                                tau=TAU, precision=prec)
         stream = torch.cuda.Stream()
         with ev.Lattice(p, rho, u, T, stream=stream.cuda_stream) as g:
-            if args.tile and prec == ev.LBM_FP32:    # fixed 16 x H (z-chunk) launch shape
+            if args.tile:                            # fixed 16 x H (z-chunk) launch shape
                 tile = tuple(int(v) for v in args.tile.split(","))
                 ev.lbm_set_tile(g.ctx, *tile)
             else:
-                tile = ev.lbm_autotune(g.ctx, 2)     # z-chunk of the fused FP32 kernel; no-op otherwise
+                tile = ev.lbm_autotune(g.ctx, 2)     # z-chunk of the fused kernel
             g.step(args.warmup)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -640,7 +651,7 @@ def run_spinodal3d(args):
             ms = e0.elapsed_time(e1) / args.steps
             launches = ev.lbm_launches_per_step(g.ctx)
             finite = bool(np.isfinite(g.conserved()).all())
-        bpl = 2 * 27 * 2 * sb
+        bpl = 2 * 27 * 2 * sb + (2 * 24 if sb == 2 else 0)
         out[name] = {"mlups": p.N / (ms * 1e-3) / 1e6, "ms_per_step": ms, "launches_per_step": launches,
                      "tile": tile,
                      "algorithmic_bytes_per_lu": bpl, "achieved_gbs": bpl * p.N / (ms * 1e-3) / 1e9,
@@ -681,6 +692,101 @@ def run_coexistence(args):
     return {"metric": "coexistence curve (Fig. 1 setting)", "unit": "lattice density", "data": "synthetic",
             "config": {"workload": "isothermal vdW slabs 384 x 4, a = 9/392/16, b = 2/21, width 8, 8000 steps, "
                                    "fused FP32 D2Q9 kernel"}, "curve": curve}
+
+
+def cs_pressure(RT, rho, a=A, b=B):
+    """p = P_E - a rho^2 of the Carnahan-Starling fluid (eta = b rho / 4)."""
+    eta = b * np.asarray(rho) / 4.0
+    return rho * RT * (1 + eta + eta**2 - eta**3) / (1 - eta) ** 3 - a * np.asarray(rho) ** 2
+
+
+def run_laplace(args):
+    """Laplace law on the fused FP32 D2Q9 kernel: isothermal Carnahan-Starling droplets at
+    T/Tc = 0.9 with 12-node interfaces (bare tau = 3), radii 36 and 48 in boxes of 2R + 40,
+    6000 steps, pressure jump time-averaged over the second half; the slope of the jump
+    against 1/R (through the origin, equimolar radius) next to the tension of a relaxed flat
+    slab on the same kernel and to the square-gradient sigma of the library's interface
+    solution (lbm_interface)."""
+    import paper_2508_00577_gb300 as ev
+    from paper_2508_00577_gb300 import inputs
+
+    width, tau, tr = 12.0, 3.0, 0.9
+    _, Tc = ev.lbm_critical_point(ev.LBM_EOS_CS, A, B)
+    RT = tr * Tc
+    rv, rl = ev.lbm_coexistence(ev.LBM_EOS_CS, A, B, RT)
+    kappa = ev.lbm_kappa_for_width(ev.LBM_EOS_CS, A, B, RT, width)
+    sigma = ev.lbm_interface(ev.LBM_EOS_CS, A, B, RT, kappa)[1]
+    n = int(12 * width) + 48
+    f = inputs.slab(n, 1, rv, rl, RT, thickness=n / 2, width=width)
+    ps = ev.lbm_params.make(nx=n, ny=1, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=kappa, tau=tau, thermal=0,
+                            precision=ev.LBM_FP32)
+    with ev.Lattice(ps, *f) as g:
+        g.step(16000)
+        rs = g.moments()[0]
+    d = 0.5 * (np.roll(rs, -1) - np.roll(rs, 1))
+    sig_m = 0.5 * kappa * float(np.sum(d * d))
+    jumps = []
+    for R in (36, 48):
+        m = 2 * R + 40
+        f = inputs.droplet(m, m, float(R), rv, rl, RT, width=width)
+        pd = ev.lbm_params.make(nx=m, ny=m, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=kappa, tau=tau, thermal=0,
+                                precision=ev.LBM_FP32)
+        acc = []
+        with ev.Lattice(pd, *f) as g:
+            for k in range(600):
+                g.step(10)
+                if k >= 300:
+                    r = g.moments()[0].reshape(m, m)
+                    c = m // 2
+                    rin, rout = r[c - 2:c + 2, c - 2:c + 2].mean(), r[0:2, :].mean()
+                    Re = np.sqrt((r.sum() - rout * m * m) / (rin - rout) / np.pi)
+                    acc.append((cs_pressure(RT, rin) - cs_pressure(RT, rout), Re))
+        dp, Re = np.mean(np.array(acc), axis=0)
+        jumps.append({"R": R, "R_equimolar": float(Re), "dp": float(dp), "dp_R_over_sigma_model": float(dp * Re / sig_m),
+                      "dp_R_over_sigma": float(dp * Re / sigma)})
+    dps = np.array([j["dp"] for j in jumps])
+    Res = np.array([j["R_equimolar"] for j in jumps])
+    slope = float(np.sum(dps / Res) / np.sum(1.0 / Res**2))
+    return {"metric": "Laplace law: slope of the pressure jump against 1/R", "value": slope, "unit": "lattice",
+            "data": "synthetic", "slope_over_sigma_model": slope / sig_m, "slope_over_sigma": slope / sigma,
+            "sigma_model": sig_m, "sigma": sigma, "jumps": jumps,
+            "config": {"workload": "isothermal CS droplets R = 36, 48, T/Tc 0.9, 12-node interfaces, tau 3, "
+                                   "6000 steps, fused FP32 D2Q9 kernel"}}
+
+
+def run_couette(args):
+    """The paper's supersonic thermal Couette flow (Fig. 2 set-up) on the fused FP32 D2Q9
+    kernel with diffusely reflecting wall nodes (lbm_set_walls): a van der Waals gas
+    (b = 0.1, a = 0.05, rho = 1, R T_w = 0.2), Ma = 1.2 at the moving wall, channel of 65
+    nodes, bare tau = 0.5, 100000 steps; the steady profile next to T(u_y) = T_w +
+    u_y (U_w - u_y) / 5 (the Navier-Stokes-Fourier solution with k = 5/2 R mu)."""
+    import paper_2508_00577_gb300 as ev
+
+    b, a, RTw, Ma, nx, tau = 0.1, 0.05, 0.2, 1.2, 66, 0.5
+    Z = 1.0 / (1.0 - b)
+    g0 = 5.0 / 3.0 * Z
+    Uw = Ma * float(np.sqrt(g0 * RTw * Z - 2 * a))        # adiabatic sound speed of p = P_E - a rho^2 at rho = 1
+    u = np.zeros((2, nx))
+    u[1, -1] = Uw
+    p = ev.lbm_params.make(nx=nx, ny=1, eos=ev.LBM_EOS_VDW, a=a, b=b, kappa=0.0, tau=tau, thermal=1,
+                           precision=ev.LBM_FP32)
+    with ev.Lattice(p, np.ones(nx), u, np.full(nx, RTw)) as g:
+        ev.lbm_set_walls(g.ctx, 1, (0, 0, 0), (0, Uw, 0), RTw)
+        g.step(100000)
+        rho, uu, T, _ = g.moments()
+    uy = uu[1]
+    fl = slice(1, nx - 1)
+    heat = Uw**2 / 20.0
+    Tu = RTw + uy * (Uw - uy) / 5.0
+    pr = rho * T / (1 - b * rho) - a * rho**2
+    cs = np.sqrt(5.0 / 3.0 / (1 - b * rho[-2]) * T[-2] / (1 - b * rho[-2]) - 2 * a * rho[-2])
+    return {"metric": "thermal Couette flow: max |T - T(u_y)| / viscous heating", "value":
+            float(np.abs(T - Tu)[fl].max() / heat), "unit": "fraction", "data": "synthetic",
+            "mach_at_moving_wall": float(uy[-2] / cs), "U_w": Uw,
+            "pressure_spread": float((pr[fl].max() - pr[fl].min()) / pr[fl].mean()),
+            "T_mid_minus_Tw_over_heating": float((T[nx // 2] - RTw) / heat),
+            "config": {"workload": "vdW gas b 0.1, a 0.05, 65-node channel, Ma 1.2, tau 0.5, 100000 steps, "
+                                   "fused FP32 D2Q9 kernel with wall nodes"}}
 
 
 def run_surrogate_kernels(args):
@@ -750,6 +856,7 @@ def main():
     ap.add_argument("--tile", default="", help="fixed launch shape W,H of the fused kernel")
     ap.add_argument("--log", default="", help="also append each result line to this JSON-lines file")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate", "surrogate_kernels", "spinodal3d",
+                                                         "laplace", "couette",
                                                            "coexistence"],
                     help="sweep: the headline droplet Laplace sweep; ensemble: 512 uneven domains; "
                          "surrogate: U-Net surrogate with lattice Boltzmann fallback vs plain LB")
@@ -779,6 +886,12 @@ def main():
         return 0
     if args.workload == "coexistence":
         emit(run_coexistence(args), args)
+        return 0
+    if args.workload == "laplace":
+        emit(run_laplace(args), args)
+        return 0
+    if args.workload == "couette":
+        emit(run_couette(args), args)
         return 0
     return run(args)
 
