@@ -486,6 +486,49 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
                     Sl[j] = sy[j] * szk;
                 }
                 const float iwz = cz ? 6.f : 1.5f;
+                if constexpr (DEV && THERMAL) {
+                    // 16-bit thermal: f and g of each source node in one pass, sharing the
+                    // source's record and its P factors (Eqs. feq, geq at the record).
+                    const float Szk = sel3(Sz, kz), pzk = sel3(pz, kz), Tzk = sel3(Tz, kz);
+                    float C[3], P[3], Dd[3];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        C[j] = ref_D(ey[j], Sy[j], ezk, Szk);
+                        P[j] = py[j] * pzk;
+                        Dd[j] = Ty[j] * pzk + py[j] * Tzk;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 9; ++j) {
+                        const int cx = j % 3 - 1, cy = j / 3 - 1;
+                        const unsigned sn = zs + cD.yo[1 - cy] + cD.xo[1 - cx];
+                        const unsigned i = (unsigned)j + 9u * (unsigned)kz;
+                        float hf = ldc(A.f, i * N + sn, 27ull * N), hg = ldc(A.g, i * N + sn, 27ull * N);
+                        {
+                            const Ref16 r = ldrec(A.Rin, sn, N);
+                            const float Px = refP(cx, r.u[0], r.th), Py = refP(cy, r.u[1], r.th);
+                            const float Pz = refP(cz, r.u[2], r.th);
+                            const float rPx = __fmul_rn(r.rho, Px), PyPz = __fmul_rn(Py, Pz);
+                            const float w = cz ? wgt16<27>(cx, cy, 1) : wgt16<27>(cx, cy, 0);
+                            const float wr = __fmul_rn(w, r.rho);
+                            hf = __fmaf_rn(wr, hf, ref_f_of(rPx, PyPz));
+                            const float ref = ref_g_of(ref_A(r.rho, r.e, Px, refS(cx, r.u[0], r.th)), rPx, PyPz,
+                                                       ref_D(Py, refS(cy, r.u[1], r.th), Pz, refS(cz, r.u[2], r.th)));
+                            hg = __fmaf_rn(__fmul_rn(wr, r.e), hg, ref);
+                        }
+                        const float iw = (cx ? 6.f : 1.5f) * (cy ? 6.f : 1.5f) * iwz;
+                        const float feq = ref_f_of(rex[cx + 1], E[cy + 1]);
+                        const float vf = kh * hf + keq * feq + kst * (rsx[cx + 1] * Sl[cy + 1]);
+                        stc(A.fo, i * N + out, 27ull * N, (vf - feq) * (inv_f * iw));
+                        const float geq = ref_g_of(Ag[cx + 1], rex[cx + 1], E[cy + 1], C[cy + 1]);
+                        float gst = As[cx + 1] * P[cy + 1] + rpx[cx + 1] * Dd[cy + 1];
+                        if (cx != 0 && cy == 0) gst += cz == 0 ? cx * hq[0] : 0.f;
+                        if (cx == 0 && cy != 0) gst += cz == 0 ? cy * hq[1] : 0.f;
+                        if (cx == 0 && cy == 0) gst += float(cz) * hq[2];
+                        const float vg = kh * hg + keq * geq + kst * gst;
+                        stc(A.go, i * N + out, 27ull * N, (vg - geq) * (inv_g * iw));
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int j = 0; j < 9; ++j) {
                     const int cx = j % 3 - 1, cy = j / 3 - 1;
