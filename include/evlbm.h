@@ -308,12 +308,20 @@ typedef struct lbm_batch lbm_batch;
 int lbm_batch_init(const lbm_params *common, int n_domains, const int *nx, const int *ny, const double *rho,
                    const double *u, const double *T, void *stream, lbm_batch **out);
 
-/* Advance every domain by n_steps >= 0 steps in one persistent launch.  Work
+/* Advance every domain by n_steps >= 0 steps in one persistent launch (or, when
+ * n_steps x work items per step would reach 2^31, in several, each of
+ * lbm_batch_launch_steps steps but the last).  Work
  * items (step, domain, tile) are taken in step-major order; an item waits, with
  * a bounded spin, for its domain's previous step.  Synchronises the stream.
  * Errors: LBM_EINVAL, LBM_ECUDA, LBM_ETIMEOUT (a wait gave up; the state is then
  * partially advanced and should be re-initialised, the batch stays usable). */
 int lbm_batch_step(lbm_batch *b, int n_steps);
+
+/* Steps one persistent launch of lbm_batch_step takes at most, for a batch with
+ * items_per_step work items per step: the largest even count whose items number
+ * fewer than 2^31 (the launch's 32-bit work counter), or 1; -1 if items_per_step < 1.
+ * Host computation, no device needed. */
+int lbm_batch_launch_steps(int items_per_step);
 
 /* Macroscopic fields of one domain (as lbm_moments): rho[N_d], u[2][N_d], T[N_d]
  * (host FP64; any may be NULL).  Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */

@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = (
     "lbm_spinodal", "lbm_interface", "lbm_step_noalloc", "lbm_batch_init", "lbm_batch_step", "lbm_batch_moments", "lbm_batch_set_tile",
     "lbm_batch_get_tile", "lbm_batch_autotune", "lbm_batch_set_wait_limit", "lbm_batch_nodes",
     "lbm_batch_free", "lbm_batch_last_error", "lbm_reset_device", "lbm_save", "lbm_load",
-    "lbm_bounds_violations", "lbm_set_walls",
+    "lbm_bounds_violations", "lbm_set_walls", "lbm_batch_launch_steps",
 )
 
 
@@ -128,6 +128,7 @@ def lib():
             L.lbm_step_noalloc.argtypes = [pp, vp, vp, vp, vp, vp, vp]
             L.lbm_batch_init.argtypes = [pp, ctypes.c_int, ip, ip, dp, dp, dp, vp, ctypes.POINTER(vp)]
             L.lbm_batch_step.argtypes = [vp, ctypes.c_int]
+            L.lbm_batch_launch_steps.argtypes = [ctypes.c_int]
             L.lbm_batch_moments.argtypes = [vp, ctypes.c_int, dp, dp, dp]
             L.lbm_batch_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             L.lbm_batch_get_tile.argtypes = [vp, ip, ip]

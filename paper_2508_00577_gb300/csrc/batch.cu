@@ -39,8 +39,8 @@ struct BatchArgs {
     const float *RT_iso;             // frozen R*T of all domains (thermal = 0)
     const BatchDomain *dom;
     int n_domains, items_per_step, n_steps;
-    unsigned long long *done;        // per-domain completed items (all steps)
-    unsigned long long *next;        // global work counter (64-bit: n_steps * items may pass 2^32)
+    unsigned *done;                  // per-domain completed items (all steps of the launch)
+    unsigned *next;                  // global work counter (n_steps * items_per_step < 2^31)
     int *error;                      // 1: a wait gave up
     const int *probe;                // test hook: a flag nothing sets (NULL = off)
     long long wait_limit;            // polls before a wait gives up
@@ -48,10 +48,10 @@ struct BatchArgs {
     float a, b, kappa, lambda, c_eq, c_star;
 };
 
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -66,18 +66,17 @@ template <int kW, bool THERMAL>
 __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_batch(BatchArgs B)
 {
     extern __shared__ v2 smem[];
-    __shared__ long long s_item;
-    __shared__ int s_dom, s_ok;
-    const unsigned long long total = (unsigned long long)B.n_steps * (unsigned long long)B.items_per_step;
+    __shared__ int s_item, s_dom, s_ok;
+    // The host splits a call so that one launch hands out fewer than 2^31 items.
+    const int total = B.n_steps * B.items_per_step;
     for (;;) {
         if (threadIdx.x == 0) {
-            long long item = -1;
-            int d = 0, ok = 0;
+            int item = -1, d = 0, ok = 0;
             if (!ld_acquire_i(B.error)) {
-                const unsigned long long g = atomicAdd(B.next, 1ull);
-                if (g < total) {
-                    item = (long long)g;
-                    const int step = (int)(item / B.items_per_step), r = (int)(item % B.items_per_step);
+                const unsigned g = atomicAdd(B.next, 1u);
+                if (g < (unsigned)total) {
+                    item = (int)g;
+                    const int step = item / B.items_per_step, r = item % B.items_per_step;
                     int lo = 0, hi = B.n_domains - 1;          // last domain with base <= r
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) / 2;
@@ -86,7 +85,7 @@ __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_batch(Bat
                     }
                     d = lo;
                     ok = 1;
-                    const unsigned long long need = (unsigned long long)step * (unsigned long long)B.dom[d].items;
+                    const unsigned need = (unsigned)step * (unsigned)B.dom[d].items;
                     long long polls = 0;
                     while (ok && ld_acquire(B.done + d) < need) {
                         if (++polls > B.wait_limit || ld_acquire_i(B.error)) ok = 0;
@@ -107,13 +106,12 @@ __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_batch(Bat
             s_ok = ok;
         }
         __syncthreads();
-        const long long item = s_item;
-        const int d = s_dom, ok = s_ok;
+        const int item = s_item, d = s_dom, ok = s_ok;
         __syncthreads();
         if (!ok) break;
-        const int step = (int)(item / B.items_per_step);
+        const int step = item / B.items_per_step;
         const BatchDomain D = B.dom[d];
-        const int k = (int)(item % B.items_per_step) - D.base;
+        const int k = item % B.items_per_step - D.base;
         FusedArgs A;
         const bool odd = step & 1;
         A.f = (odd ? B.popB_f : B.popA_f) + D.off;
@@ -140,7 +138,7 @@ __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_batch(Bat
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(B.done + d, 1ull);
+            atomicAdd(B.done + d, 1u);
         }
     }
 }
@@ -216,7 +214,7 @@ struct lbm_batch {
     float *RT_iso;
     int cur;
     BatchDomain *d_dom;
-    unsigned long long *d_done, *d_next;
+    unsigned *d_done, *d_next;
     int *d_error, *d_probe;
     int tile_w, tile_h;
     long long wait_limit;
@@ -310,8 +308,8 @@ BatchArgs make_args(const lbm_batch *b, int n_steps)
 
 cudaError_t enqueue(lbm_batch *b, int n_steps)
 {
-    cudaError_t e = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned long long) * b->n, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), b->stream);
+    cudaError_t e = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned) * b->n, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_error, 0, sizeof(int), b->stream);
     if (e != cudaSuccess) return e;
     const BatchArgs B = make_args(b, n_steps);
@@ -378,6 +376,22 @@ void free_batch(lbm_batch *b)
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     b->stream = nullptr;
 }
+
+}  // namespace
+
+// Steps one persistent launch may take: its work counter hands out n_steps x
+// items_per_step items as 32-bit values (kept below 2^31); an even count keeps the
+// buffer parity, so the captured graph of a long call is reused for every launch.
+extern "C" int lbm_batch_launch_steps(int items_per_step)
+{
+    if (items_per_step < 1) return -1;
+    const long long per = ((1LL << 31) - 1) / items_per_step;
+    return per >= 2 ? (int)(per & ~1LL) : 1;
+}
+
+namespace {
+
+int batch_launch_steps(int items_per_step) { return lbm_batch_launch_steps(items_per_step); }
 
 KParams domain_kparams(const lbm_batch *b, int d)
 {
@@ -464,8 +478,8 @@ int lbm_batch_init(const lbm_params *p, int n_domains, const int *nx, const int 
     }
     if (e == cudaSuccess) e = cudaMalloc(&b->RT_iso, sizeof(float) * nodes);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_dom, sizeof(BatchDomain) * n_domains);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_done, sizeof(unsigned long long) * n_domains);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_done, sizeof(unsigned) * n_domains);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_error, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_probe, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_probe, 0, sizeof(int), b->stream);
@@ -523,11 +537,15 @@ int lbm_batch_step(lbm_batch *b, int n_steps)
 {
     evtrace::Range trace_("lbm_batch_step");
     if (!b || n_steps < 0) return LBM_EINVAL;
-    if (n_steps == 0) return LBM_OK;
-    const int rc = run_graph(b, n_steps);
-    if (rc) return rc;
-    b->cur ^= (n_steps & 1);
-    b->steps += n_steps;
+    int left = n_steps;
+    while (left > 0) {
+        const int n = left < batch_launch_steps(b->items_per_step) ? left : batch_launch_steps(b->items_per_step);
+        const int rc = run_graph(b, n);
+        if (rc) return rc;
+        b->cur ^= (n & 1);
+        b->steps += n;
+        left -= n;
+    }
     return LBM_OK;
 }
 

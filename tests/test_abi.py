@@ -194,3 +194,22 @@ def test_surrogate_binding_constants_match_header():
     assert len(vals) >= 18
     for name, value in vals.items():
         assert getattr(S, name) == int(value), name
+
+
+def test_batch_split_keeps_launch_items_below_2_31():
+    """lbm_batch_step splits a call whose n_steps x items per step would overflow the
+    persistent launch's 32-bit work counter: every launch but the last takes
+    lbm_batch_launch_steps steps, an even count (the buffer parity, and so the captured
+    graph, stays the same) whose items number fewer than 2^31."""
+    L = ev.lib()
+    for items in (1, 2, 3, 3001, 65536, 2**20 + 7, 2**30 - 1, 2**30 + 1, 2**31 - 1):
+        n = L.lbm_batch_launch_steps(items)
+        assert n >= 1
+        assert n * items < 2**31, items
+        assert n == 1 or n % 2 == 0
+        assert n == 1 or (n + 2) * items >= 2**31 - 1      # the largest such even count
+    assert L.lbm_batch_launch_steps(0) == -1
+    # a call of INT_MAX steps on the ensemble's ~3000 items per step: a few thousand launches
+    n = L.lbm_batch_launch_steps(3000)
+    launches = -(-(2**31 - 1) // n)
+    assert 2000 < launches < 4000
