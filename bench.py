@@ -845,7 +845,7 @@ def peaks_bf16():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 2000; ensemble: its full 5000)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--layers", type=int, default=9, help="layers of the sweep (9 = the full workload)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
@@ -869,6 +869,8 @@ def main():
     ap.add_argument("--max-mass-drift", type=float, default=1e-3)
     ap.add_argument("--area-sweep", type=float, nargs="+", default=[0.02, 0.005, 0.001])
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = ENSEMBLE_STEPS if args.workload == "ensemble" and args.impl == "native" else 2000
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "ensemble":

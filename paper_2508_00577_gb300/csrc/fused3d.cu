@@ -15,17 +15,18 @@
 //   A: rho, j (plane q)            pulled f           on the tile + 3 halo columns (22 x 22)
 //   B: Korteweg stress (q-1)       rho of q-2..q      on the tile + 2 (20 x 20)
 //   C: F, u, T, EOS (q-2)          stress of q-3..q-1, pulled g   (18 x 18)
-//   D: collide (q-3)               u, T fields of q-4..q-2, populations pulled
-//                                  again (L2 hits: stage A/C read them 3/1 planes ago)
+//   D: collide (q-3)               u, T fields of q-4..q-2, the tile's pulled f from
+//                                  the TMEM stash stage A wrote 3 planes ago, pulled g
+//                                  again (L2 hits: stage C read them 1 plane ago)
 // Shared fields live in 3-deep plane rings sized to the region that reads them;
 // centre values pass from C to D through a one-plane per-thread slot (stage C takes
 // the tile column a thread collides in D first, and reads the slot before rewriting
-// it); at 80.7 KB per CTA two CTAs leave the L1 ~92 KB for loads in flight.
+// it); at 73.1 KB per CTA two CTAs leave the L1 ~92 KB for loads in flight.
 //
-// 16-bit storage: every pulled population is rebuilt from its source node's
-// reference record (one 16-byte load per pulled population, L1/L2 hits after the
-// first) and the stored deviation; stage D writes the node's new record and the
-// deviations of its populations from the record's equilibria.
+// 16-bit storage: every pulled population is rebuilt from its source node's FP32
+// reference record (a 16- and an 8-byte load, L1/L2 hits after the first) and the
+// stored deviation; stage D writes the node's new record and the deviations of its
+// populations from the equilibria it computed for the collision.
 #include "bounds.cuh"
 #include "dev16.cuh"
 #include "dispatch.h"
@@ -67,6 +68,49 @@ __device__ __forceinline__ float rcpa(float a)
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
     return r;
+}
+
+// Tensor memory as a per-thread stash (no tensor-core work here).  Stage A pulls the 27 f
+// of the thread's own tile column three planes before stage D collides that node; the
+// values wait in TMEM instead of being pulled from L2/DRAM a second time.  4 plane slots
+// of 32 columns per thread; the two warps of a lane quarter (w and w + 4) use column halves
+// 0..127 and 128..255 of the CTA's 256 columns (two CTAs per SM fill the 512).  In a slot,
+// population i = 9 kz + j sits at column 8 kz + j for j < 8 and at 24 + kz for j = 8, so
+// that every access starts at a multiple of its width.
+constexpr int TM_COLS = 256, TM_SLOT = 32, TM_SLOTS = 4;
+static_assert(TM_SLOTS * TM_SLOT <= TM_COLS / 2, "stash slots exceed a warp's column half");
+
+__device__ __forceinline__ uint32_t tm_addr(uint32_t base, int t)
+{
+    const int w = t >> 5;
+    return base + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)((w >> 2) * (TM_COLS / 2));
+}
+// Warp-collective (.sync.aligned): every thread of the warp executes these, converged.
+__device__ __forceinline__ void tm_st27(uint32_t ta, const float v[27])
+{
+#define R_(k) "r"(__float_as_uint(v[k]))
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(ta), R_(0), R_(1), R_(2), R_(3), R_(4), R_(5), R_(6), R_(7), R_(9), R_(10), R_(11), R_(12),
+                 R_(13), R_(14), R_(15), R_(16) : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(ta + 16), R_(18), R_(19), R_(20), R_(21), R_(22), R_(23), R_(24), R_(25) : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
+                 ::"r"(ta + 24), R_(8), R_(17), R_(26), "r"(0u) : "memory");
+#undef R_
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// The nine populations of layer kz, waited for before they are used.
+__device__ __forceinline__ void tm_ld9(uint32_t ta, int kz, float v[9])
+{
+    uint32_t r[9];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%9];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%8}, [%10];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8])
+                 : "r"(ta + 8u * (uint32_t)kz), "r"(ta + 24u + (uint32_t)kz) : "memory");
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = __uint_as_float(r[k]);
 }
 
 // Global loads and stores with the bounds check of checked builds (no-op otherwise).
@@ -169,7 +213,17 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
     const float a = A.a, b = A.b, kappa = A.kappa, lambda = A.lambda;
 
     // Columns this thread handles in stages A, B, C (up to two each).
-    auto colA = [&](int k, int &cx, int &cy) { const int c = t + k * NT; cx = c % WA - 3; cy = c / WA - 3; return c < SA; };
+    // Stage A: first the thread's own tile column (whose pulled f it stashes for stage D),
+    // then the 228 halo columns on threads 0..227: three rows above and below the tile
+    // (22 columns each), then three columns left and right of each tile row.
+    auto colA = [&](int k, int &cx, int &cy) {
+        if (k == 0) { cx = t % TX; cy = t / TX; return true; }
+        const int r = t;
+        if (r < 3 * WA) { cx = r % WA - 3; cy = r / WA - 3; }
+        else if (r < 6 * WA) { cx = (r - 3 * WA) % WA - 3; cy = TY + (r - 3 * WA) / WA; }
+        else { const int m = (r - 6 * WA) % 6; cy = (r - 6 * WA) / 6; cx = m < 3 ? m - 3 : TX + m - 3; }
+        return r < SA - NT;
+    };
     auto colB = [&](int k, int &cx, int &cy) { const int c = t + k * NT; cx = c % WB - 2; cy = c / WB - 2; return c < SB; };
     // Stage C: first the tile's own column of this thread (the one it collides in stage D,
     // so the centre values stay thread-private), then the 68 ring columns on threads 0..67.
@@ -191,6 +245,18 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
     const bool inD = x0 + dcx < nx && y0 + dcy < ny;
     const Cell cD = cell_of(x0 + dcx, y0 + dcy, nx, ny);
 
+    // TMEM stash of the tile's pulled f (allocated by warp 0, freed after the last plane).
+    __shared__ uint32_t tm_base_sh;
+    if (t < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"((uint32_t)__cvta_generic_to_shared(&tm_base_sh)), "r"(TM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmt = tm_addr(tm_base_sh, t);
+
     const int qbeg = z0 - 3, qend = zend + 2;
     for (int q = qbeg; q <= qend; ++q) {
         const int s0 = ((q % 3) + 3) % 3;                 // ring slot of plane q (and of q-3)
@@ -200,22 +266,25 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
         if (q <= zend + 2) {
             unsigned zo[3];
             plane_offsets(q, nx, ny, nz, zo);
-#pragma unroll
+#pragma unroll 1
             for (int k = 0; k < 2; ++k) {
                 int cx, cy;
                 if (!colA(k, cx, cy)) continue;
                 const Cell c = cell_of(x0 + cx, y0 + cy, nx, ny);
                 float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+                float hv[27];
 #pragma unroll
                 for (int i = 0; i < 27; ++i) {
                     const unsigned si = src_of(i, c, zo, N);
                     float h = ldc(A.f, si, 27ull * N);
                     if constexpr (DEV) h = decode_f<27>(cxi(i), cyi(i), czi(i), ldrec(A.Rin, si - i * N, N), h);
+                    hv[i] = h;
                     rho += h;
                     if (cxi(i) == 1) jx += h; else if (cxi(i) == -1) jx -= h;
                     if (cyi(i) == 1) jy += h; else if (cyi(i) == -1) jy -= h;
                     if (czi(i) == 1) jz += h; else if (czi(i) == -1) jz -= h;
                 }
+                if (k == 0) tm_st27(tmt + (uint32_t)(((q + 4) & 3) * TM_SLOT), hv);     // all threads: slot of plane q
                 if (in_bounds(sa(cx, cy), SA)) RHO[s0 * SA + sa(cx, cy)] = rho;
                 if (cx >= -1 && cx <= TX && cy >= -1 && cy <= TY && in_bounds(sc(cx, cy), SC)) {
                     float *jr = J + s0 * 3 * SC + sc(cx, cy);
@@ -378,7 +447,11 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
 
         // ---------------- D: collide plane q-3 ----------------
         const int p = q - 3;
-        if (p >= z0 && p < zend && inD && in_bounds(sc(dcx, dcy) - WC, SC) && in_bounds(sc(dcx, dcy) + WC, SC)) {
+        if (p >= z0 && p < zend) {
+            // Every thread runs stage D (the TMEM loads are warp-collective); threads whose
+            // column lies outside the lattice compute on wrapped values and store nothing.
+            const bool act = inD && in_bounds(sc(dcx, dcy) - WC, SC) && in_bounds(sc(dcx, dcy) + WC, SC);
+            const uint32_t tmp = tmt + (uint32_t)(((p + 4) & 3) * TM_SLOT);       // stash slot of plane p
             // Centre values of plane p (stage C ran at iteration q-1), read in stage C.
             const float rho = cprev[0], Fx = cprev[1], Fy = cprev[2], Fz = cprev[3];
             const float RT = cprev[4], th = cprev[5], g0 = cprev[6];
@@ -432,7 +505,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
             // deviations written are taken against the equilibria computed here from it.
             float inv_f = 0.f, inv_g = 0.f;
             if constexpr (DEV) {
-                if (in_bounds(out, N)) {
+                if (act && in_bounds(out, N)) {
                     __stcs(reinterpret_cast<float4 *>(A.Rout) + out, make_float4(rho, ux, uy, uz));
                     __stcs(reinterpret_cast<float2 *>(A.Rout + 4ull * N) + out, make_float2(th, e));
                 }
@@ -486,6 +559,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
                     Sl[j] = sy[j] * szk;
                 }
                 const float iwz = cz ? 6.f : 1.5f;
+                float hf9[9];                                 // pulled f of this layer (stage A's stash)
+                tm_ld9(tmp, kz, hf9);
                 if constexpr (DEV && THERMAL) {
                     // 16-bit thermal: f and g of each source node in one pass, sharing the
                     // source's record and its P factors (Eqs. feq, geq at the record).
@@ -502,7 +577,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
                         const int cx = j % 3 - 1, cy = j / 3 - 1;
                         const unsigned sn = zs + cD.yo[1 - cy] + cD.xo[1 - cx];
                         const unsigned i = (unsigned)j + 9u * (unsigned)kz;
-                        float hf = ldc(A.f, i * N + sn, 27ull * N), hg = ldc(A.g, i * N + sn, 27ull * N);
+                        const float hf = hf9[j];
+                        float hg = ldc(A.g, i * N + sn, 27ull * N);
                         {
                             const Ref16 r = ldrec(A.Rin, sn, N);
                             const float Px = refP(cx, r.u[0], r.th), Py = refP(cy, r.u[1], r.th);
@@ -510,7 +586,6 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
                             const float rPx = __fmul_rn(r.rho, Px), PyPz = __fmul_rn(Py, Pz);
                             const float w = cz ? wgt16<27>(cx, cy, 1) : wgt16<27>(cx, cy, 0);
                             const float wr = __fmul_rn(w, r.rho);
-                            hf = __fmaf_rn(wr, hf, ref_f_of(rPx, PyPz));
                             const float ref = ref_g_of(ref_A(r.rho, r.e, Px, refS(cx, r.u[0], r.th)), rPx, PyPz,
                                                        ref_D(Py, refS(cy, r.u[1], r.th), Pz, refS(cz, r.u[2], r.th)));
                             hg = __fmaf_rn(__fmul_rn(wr, r.e), hg, ref);
@@ -518,77 +593,62 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
                         const float iw = (cx ? 6.f : 1.5f) * (cy ? 6.f : 1.5f) * iwz;
                         const float feq = ref_f_of(rex[cx + 1], E[cy + 1]);
                         const float vf = kh * hf + keq * feq + kst * (rsx[cx + 1] * Sl[cy + 1]);
-                        stc(A.fo, i * N + out, 27ull * N, (vf - feq) * (inv_f * iw));
+                        if (act) stc(A.fo, i * N + out, 27ull * N, (vf - feq) * (inv_f * iw));
                         const float geq = ref_g_of(Ag[cx + 1], rex[cx + 1], E[cy + 1], C[cy + 1]);
                         float gst = As[cx + 1] * P[cy + 1] + rpx[cx + 1] * Dd[cy + 1];
                         if (cx != 0 && cy == 0) gst += cz == 0 ? cx * hq[0] : 0.f;
                         if (cx == 0 && cy != 0) gst += cz == 0 ? cy * hq[1] : 0.f;
                         if (cx == 0 && cy == 0) gst += float(cz) * hq[2];
                         const float vg = kh * hg + keq * geq + kst * gst;
-                        stc(A.go, i * N + out, 27ull * N, (vg - geq) * (inv_g * iw));
+                        if (act) stc(A.go, i * N + out, 27ull * N, (vg - geq) * (inv_g * iw));
                     }
-                    continue;
-                }
-#pragma unroll
-                for (int j = 0; j < 9; ++j) {
-                    const int cx = j % 3 - 1, cy = j / 3 - 1;
-                    const unsigned sn = zs + cD.yo[1 - cy] + cD.xo[1 - cx];       // source node
-                    const unsigned i = (unsigned)j + 9u * (unsigned)kz;
-                    // The output is not read again this step: a streaming store keeps L2 for
-                    // the populations the stages still share.
-                    float h = ldc(A.f, i * N + sn, 27ull * N);
-                    if constexpr (DEV) {
-                        const Ref16 r = ldrec(A.Rin, sn, N);
-                        const float rPx = __fmul_rn(r.rho, refP(cx, r.u[0], r.th));
-                        const float PyPz = __fmul_rn(refP(cy, r.u[1], r.th), refP(cz, r.u[2], r.th));
-                        const float w = cz ? wgt16<27>(cx, cy, 1) : wgt16<27>(cx, cy, 0);
-                        h = __fmaf_rn(__fmul_rn(w, r.rho), h, ref_f_of(rPx, PyPz));
-                    }
-                    const float feq = ref_f_of(rex[cx + 1], E[cy + 1]);
-                    float v = kh * h + keq * feq + kst * (rsx[cx + 1] * Sl[cy + 1]);
-                    if constexpr (DEV)
-                        v = (v - feq) * (inv_f * ((cx ? 6.f : 1.5f) * (cy ? 6.f : 1.5f) * iwz));
-                    stc(A.fo, i * N + out, 27ull * N, v);
-                }
-                if (THERMAL) {
-                    const float Szk = sel3(Sz, kz), pzk = sel3(pz, kz), Tzk = sel3(Tz, kz);
-                    float C[3], P[3], Dd[3];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        C[j] = ref_D(ey[j], Sy[j], ezk, Szk);
-                        P[j] = py[j] * pzk;
-                        Dd[j] = Ty[j] * pzk + py[j] * Tzk;
-                    }
+                } else {
 #pragma unroll
                     for (int j = 0; j < 9; ++j) {
                         const int cx = j % 3 - 1, cy = j / 3 - 1;
-                        const unsigned sn = zs + cD.yo[1 - cy] + cD.xo[1 - cx];
                         const unsigned i = (unsigned)j + 9u * (unsigned)kz;
-                        float h = ldc(A.g, i * N + sn, 27ull * N);
-                        if constexpr (DEV) {
-                            const Ref16 r = ldrec(A.Rin, sn, N);
-                            const float Px = refP(cx, r.u[0], r.th), Py = refP(cy, r.u[1], r.th);
-                            const float Pz = refP(cz, r.u[2], r.th);
-                            const float ref = ref_g_of(ref_A(r.rho, r.e, Px, refS(cx, r.u[0], r.th)),
-                                                       __fmul_rn(r.rho, Px), __fmul_rn(Py, Pz),
-                                                       ref_D(Py, refS(cy, r.u[1], r.th), Pz, refS(cz, r.u[2], r.th)));
-                            const float w = cz ? wgt16<27>(cx, cy, 1) : wgt16<27>(cx, cy, 0);
-                            h = __fmaf_rn(__fmul_rn(__fmul_rn(w, r.rho), r.e), h, ref);
-                        }
-                        const float geq = ref_g_of(Ag[cx + 1], rex[cx + 1], E[cy + 1], C[cy + 1]);
-                        float gst = As[cx + 1] * P[cy + 1] + rpx[cx + 1] * Dd[cy + 1];
-                        // g' on the |c| = 1 populations
-                        if (cx != 0 && cy == 0) gst += cz == 0 ? cx * hq[0] : 0.f;
-                        if (cx == 0 && cy != 0) gst += cz == 0 ? cy * hq[1] : 0.f;
-                        if (cx == 0 && cy == 0) gst += float(cz) * hq[2];
-                        float v = kh * h + keq * geq + kst * gst;
+                        const float h = hf9[j];
+                        const float feq = ref_f_of(rex[cx + 1], E[cy + 1]);
+                        float v = kh * h + keq * feq + kst * (rsx[cx + 1] * Sl[cy + 1]);
                         if constexpr (DEV)
-                            v = (v - geq) * (inv_g * ((cx ? 6.f : 1.5f) * (cy ? 6.f : 1.5f) * iwz));
-                        stc(A.go, i * N + out, 27ull * N, v);
+                            v = (v - feq) * (inv_f * ((cx ? 6.f : 1.5f) * (cy ? 6.f : 1.5f) * iwz));
+                        // The output is not read again this step: a streaming store keeps L2 for
+                        // the populations the stages still share.
+                        if (act) stc(A.fo, i * N + out, 27ull * N, v);
+                    }
+                    if (THERMAL) {
+                        const float Szk = sel3(Sz, kz), pzk = sel3(pz, kz), Tzk = sel3(Tz, kz);
+                        float C[3], P[3], Dd[3];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            C[j] = ref_D(ey[j], Sy[j], ezk, Szk);
+                            P[j] = py[j] * pzk;
+                            Dd[j] = Ty[j] * pzk + py[j] * Tzk;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 9; ++j) {
+                            const int cx = j % 3 - 1, cy = j / 3 - 1;
+                            const unsigned sn = zs + cD.yo[1 - cy] + cD.xo[1 - cx];
+                            const unsigned i = (unsigned)j + 9u * (unsigned)kz;
+                            const float h = ldc(A.g, i * N + sn, 27ull * N);       // FP32 storage here
+                            const float geq = ref_g_of(Ag[cx + 1], rex[cx + 1], E[cy + 1], C[cy + 1]);
+                            float gst = As[cx + 1] * P[cy + 1] + rpx[cx + 1] * Dd[cy + 1];
+                            // g' on the |c| = 1 populations
+                            if (cx != 0 && cy == 0) gst += cz == 0 ? cx * hq[0] : 0.f;
+                            if (cx == 0 && cy != 0) gst += cz == 0 ? cy * hq[1] : 0.f;
+                            if (cx == 0 && cy == 0) gst += float(cz) * hq[2];
+                            if (act) stc(A.go, i * N + out, 27ull * N, kh * h + keq * geq + kst * gst);
+                        }
                     }
                 }
             }
         }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (t < 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm_base_sh), "r"(TM_COLS));
     }
 }
 
