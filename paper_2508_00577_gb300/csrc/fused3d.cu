@@ -30,6 +30,7 @@
 #include "bounds.cuh"
 #include "dev16.cuh"
 #include "dispatch.h"
+#include "tmem.cuh"
 
 namespace evlbm {
 
@@ -83,11 +84,13 @@ static_assert(TM_SLOTS * TM_SLOT <= TM_COLS / 2, "stash slots exceed a warp's co
 __device__ __forceinline__ uint32_t tm_addr(uint32_t base, int t)
 {
     const int w = t >> 5;
-    return base + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)((w >> 2) * (TM_COLS / 2));
+    return tmem::lane_base(base, w) + (uint32_t)((w >> 2) * (TM_COLS / 2));
 }
-// Warp-collective (.sync.aligned): every thread of the warp executes these, converged.
+// Warp-collective (.sync.aligned): every thread of the warp executes these (they
+// reconverge the warp first).
 __device__ __forceinline__ void tm_st27(uint32_t ta, const float v[27])
 {
+    __syncwarp();
 #define R_(k) "r"(__float_as_uint(v[k]))
     asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
                  ::"r"(ta), R_(0), R_(1), R_(2), R_(3), R_(4), R_(5), R_(6), R_(7), R_(9), R_(10), R_(11), R_(12),
@@ -102,6 +105,7 @@ __device__ __forceinline__ void tm_st27(uint32_t ta, const float v[27])
 // The nine populations of layer kz, waited for before they are used.
 __device__ __forceinline__ void tm_ld9(uint32_t ta, int kz, float v[9])
 {
+    __syncwarp();
     uint32_t r[9];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%9];\n\t"
                  "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%8}, [%10];\n\t"
@@ -247,14 +251,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
 
     // TMEM stash of the tile's pulled f (allocated by warp 0, freed after the last plane).
     __shared__ uint32_t tm_base_sh;
-    if (t < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"((uint32_t)__cvta_generic_to_shared(&tm_base_sh)), "r"(TM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (t < 32) tmem::alloc(&tm_base_sh, TM_COLS);
+    tmem::fence_sync();
     const uint32_t tmt = tm_addr(tm_base_sh, t);
 
     const int qbeg = z0 - 3, qend = zend + 2;
@@ -644,12 +642,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (t < 32) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm_base_sh), "r"(TM_COLS));
-    }
+    tmem::fence_sync();
+    if (t < 32) tmem::dealloc(tm_base_sh, TM_COLS);
 }
 
 template <bool THERMAL, typename S>
