@@ -328,7 +328,11 @@ def run(args):
         "config": {"workload": WORKLOAD if nz == 9 else f"{nz} of the 9 layers of: {WORKLOAD}", "nodes_per_gpu": N, "layers": nz, "lattice": "D2Q9",
                    "thermal": True, "precision": "fp32", "l2": "inputs larger than L2 (1.36 GB/step)",
                    "tile": {"w": tile[0], "h": tile[1], "autotuned": not (args.no_autotune or args.tile)},
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "quoted_on": "the 2-D static-droplet Laplace sweep (1024^2 periodic, FP32, T/Tc in {0.7, 0.8, "
+                                "0.9} x R in {64, 128, 256}, one layer each), the workload the MLUPS headline is "
+                                "quoted on; the 256^3 D3Q27 spinodal (FP32/FP16/BF16) and the 512-domain ensemble "
+                                "follow as sub-lines of the same run"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": (MEASURED_TRAFFIC_BYTES[tuple(tile)] / 1e9

@@ -213,7 +213,7 @@ def forward(P, x_fields, B, H, W, norm):
 
 def loss_and_grad(P, x_fields, y_fields, B, H, W, norm):
     """Loss = mean over pixels and channels of (o - (y - x)/out_scale)^2, and
-    its gradient as a dict shaped like P (plus 'x' for the input fields)."""
+    its gradient as a dict shaped like P."""
     out_scale = np.asarray(norm[2], dtype=np.float64)
     o, c = forward(P, x_fields, B, H, W, norm)
     x = fields_to_nhwc(x_fields, B, H, W)
@@ -221,7 +221,14 @@ def loss_and_grad(P, x_fields, y_fields, B, H, W, norm):
     r = o - (y - x) / out_scale
     n = r.size
     loss = float((r * r).sum() / n)
-    do = 2.0 * r / n
+    G, _ = backward(P, c, 2.0 * r / n)
+    return loss, G, o
+
+
+def backward(P, c, do, need_dxin=False):
+    """Gradients of the parameters given do = dL/do [B][H][W][4] and the cache of
+    forward; with need_dxin also dL/dxin, the gradient in the normalised input
+    [B][H][W][8] (channels 4..7 are the zero padding)."""
     G = {"hW": do.reshape(-1, 4).T @ c["y03"].reshape(-1, BASE), "hb": do.reshape(-1, 4).sum(0)}
     dy = do @ P["hW"]
 
@@ -253,8 +260,37 @@ def loss_and_grad(P, x_fields, y_fields, B, H, W, norm):
     dp0 = conv_b(2, d10)
     d01 = dcat0[..., :32] + pool2_bwd(dp0)
     d00 = conv_b(1, d01)
-    conv_b(0, d00, need_dx=False)
-    return loss, G, o
+    dxin = conv_b(0, d00, need_dx=need_dxin)
+    return G, dxin
+
+
+def unrolled_loss_and_grad(P, x0_fields, targets, B, H, W, norm):
+    """Training loss of k windows applied to the network's own predictions:
+    x'_0 = x_0, x'_{j+1} = x'_j + out_scale * o(x'_j), and
+    L = (1/k) sum_{j=1..k} mean over pixels and channels of ((x'_j - y_j)/out_scale)^2
+    for targets y_1..y_k (planar [k][4][B*H*W]); k = 1 is loss_and_grad.  Returns
+    (L, gradient dict shaped like P, dL/dx_0 planar [4][B*H*W]).  Backpropagation
+    through the chain: dL/dx'_j = (its loss term) + dL/dx'_{j+1} (the identity path)
+    + the network path, whose input gradient is dL/dxin / in_scale."""
+    _, in_scale, out_scale = (np.asarray(v, dtype=np.float64) for v in norm)
+    k = len(targets)
+    xs = [np.asarray(x0_fields, dtype=np.float64)]
+    for _ in range(k):
+        xs.append(predict(P, xs[-1], B, H, W, norm))
+    n = 4 * B * H * W
+    loss = 0.0
+    Gx = np.zeros((4, B * H * W))                     # dL/dx'_j, planar
+    Gsum = None
+    for j in range(k, 0, -1):
+        r = (xs[j] - np.asarray(targets[j - 1], dtype=np.float64)) / out_scale[:, None]
+        loss += float((r * r).sum()) / (n * k)
+        Gx = Gx + 2.0 * r / out_scale[:, None] / (n * k)
+        _, c = forward(P, xs[j - 1], B, H, W, norm)
+        do = fields_to_nhwc(Gx * out_scale[:, None], B, H, W)      # x'_j = x'_{j-1} + out_scale o
+        G, dxin = backward(P, c, do, need_dxin=True)
+        Gsum = G if Gsum is None else {key: Gsum[key] + G[key] for key in G}
+        Gx = Gx + nhwc_to_fields(dxin[..., :4]) / in_scale[:, None]
+    return loss, Gsum, Gx
 
 
 def predict(P, x_fields, B, H, W, norm):

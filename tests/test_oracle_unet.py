@@ -145,6 +145,60 @@ def test_loss_gradient_against_finite_differences():
     assert checked == 2 * len(keys)
 
 
+def _unrolled_loss(P, x0, targets, B, H, W):
+    xs = np.asarray(x0, dtype=np.float64)
+    out_scale = NORM[2][:, None]
+    loss = 0.0
+    for yj in targets:
+        xs = U.predict(P, xs, B, H, W, NORM)
+        r = (xs - yj) / out_scale
+        loss += float((r * r).mean()) / len(targets)
+    return loss
+
+
+def test_unrolled_single_window_is_the_window_loss():
+    B, H, W = 2, 16, 16
+    P, _ = rand_params()
+    x, y = _fields(B, H, W)
+    l1, G1, _ = U.loss_and_grad(P, x, y, B, H, W, NORM)
+    lu, Gu, _ = U.unrolled_loss_and_grad(P, x, [y], B, H, W, NORM)
+    assert abs(lu - l1) <= 1e-12 * l1
+    for k in G1:
+        np.testing.assert_allclose(Gu[k], G1[k], rtol=1e-10, atol=1e-14 * np.abs(G1[k]).max())
+
+
+def test_unrolled_gradient_against_finite_differences():
+    """Three windows chained through the network: the gradient in the parameters (one
+    entry of every tensor) and in the start fields (three entries) against central
+    differences of the unrolled loss, evaluated with predict() alone."""
+    B, H, W = 1, 16, 16
+    P, _ = rand_params(scale=1.0)
+    x, _ = _fields(B, H, W)
+    targets = [x + 0.01 * (j + 1) * rng.normal(size=x.shape) * np.array([[0.05], [0.01], [0.01], [0.001]])
+               for j in range(3)]
+    loss, G, Gx = U.unrolled_loss_and_grad(P, x, targets, B, H, W, NORM)
+    assert abs(loss - _unrolled_loss(P, x, targets, B, H, W)) <= 1e-12 * loss
+    keys = [k for k in P if not k.startswith("_")]
+    for k in keys:
+        idx = tuple(rng.integers(0, s) for s in P[k].shape)
+        h = 1e-6 * max(1.0, abs(P[k][idx]))
+        old = P[k][idx]
+        P[k][idx] = old + h
+        lp = _unrolled_loss(P, x, targets, B, H, W)
+        P[k][idx] = old - h
+        lm = _unrolled_loss(P, x, targets, B, H, W)
+        P[k][idx] = old
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - G[k][idx]) <= 1e-5 * abs(G[k][idx]) + 1e-9 * loss, (k, idx, fd, G[k][idx])
+    for c, m in ((0, 5), (2, 77), (3, 200)):
+        h = 1e-7 * max(abs(x[c, m]), NORM[1][c])
+        xp, xm = x.copy(), x.copy()
+        xp[c, m] += h
+        xm[c, m] -= h
+        fd = (_unrolled_loss(P, xp, targets, B, H, W) - _unrolled_loss(P, xm, targets, B, H, W)) / (2 * h)
+        assert abs(fd - Gx[c, m]) <= 1e-5 * abs(Gx[c, m]) + 1e-7 * loss / NORM[1][c], (c, m, fd, Gx[c, m])
+
+
 def test_translation_equivariance():
     B, H, W = 1, 32, 32
     P, _ = rand_params()
