@@ -511,9 +511,19 @@ def run_surrogate(args):
         yb = v[w + 1, :, d, :].permute(1, 0, 2).reshape(4, -1).contiguous()
         return xb, yb
 
+    def sequence(v, w, d, k):
+        """Start fields of windows w and the k following states, [k][4][bs*Mb] targets."""
+        w = torch.as_tensor(w, device=dev)
+        d = torch.as_tensor(d, device=dev)
+        x0 = v[w, :, d, :].permute(1, 0, 2).reshape(4, -1).contiguous()
+        tg = torch.stack([v[w + j, :, d, :].permute(1, 0, 2).reshape(4, -1) for j in range(1, k + 1)]).contiguous()
+        return x0, tg
+
     # A fixed validation batch from the first held-out domains, windows spread over the run.
     val = trajectories(test_doms[:8]).reshape(SUR_WINDOWS + 1, 4, 8, Mb)
     vx, vy = batch(val, np.arange(0, SUR_WINDOWS, SUR_WINDOWS // bs)[:bs], np.arange(bs) % 8)
+    K = max(1, args.unroll)
+    vsx, vst = sequence(val, np.arange(0, SUR_WINDOWS - K, (SUR_WINDOWS - K) // bs)[:bs], np.arange(bs) % 8, K)
     del val
     rng = np.random.default_rng(0)
     model = S.Surrogate(SUR_N, SUR_N, seed=3)
@@ -532,7 +542,24 @@ def run_surrogate(args):
             losses.append((it, round(loss, 5), round(model.forward_backward(vx.data_ptr(), vy.data_ptr(), bs), 5)))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    del snaps, view, x, y, vx, vy
+
+    # Unrolled fine-tuning: K windows applied to the network's own predictions, so that the
+    # training sees (and is penalised for) the error it accumulates over a rollout.
+    def val_losses():
+        return (round(model.forward_backward(vx.data_ptr(), vy.data_ptr(), bs), 5),
+                round(model.forward_backward_unrolled(vsx.data_ptr(), vst.data_ptr(), K, bs), 5))
+    unrolled = {"windows": K, "steps": args.unroll_steps, "val_before": val_losses()}
+    t0 = time.perf_counter()
+    for it in range(args.unroll_steps):
+        x0, tg = sequence(view, rng.integers(0, SUR_WINDOWS - K + 1, bs), rng.integers(0, len(train_doms), bs), K)
+        torch.cuda.synchronize()
+        lr = 0.3 * args.lr * 0.5 * (1 + np.cos(np.pi * it / args.unroll_steps))
+        model.train_step_unrolled(x0.data_ptr(), tg.data_ptr(), K, bs, float(lr), want_loss=False)
+    torch.cuda.synchronize()
+    unrolled["seconds"] = time.perf_counter() - t0
+    unrolled["val_after"] = val_losses()
+    unrolled["val_note"] = f"(one-window loss, {K}-window unrolled loss) on held-out windows"
+    del snaps, view, x, y, vx, vy, vsx, vst
 
     # Held-out domains: the plain lattice Boltzmann run is the reference every error is measured against.
     nd = len(test_doms)
@@ -610,6 +637,7 @@ def run_surrogate(args):
         "rollouts": results,
         "inference": {"ms_per_window": t_inf * 1e3, "tflops": flops / t_inf / 1e12, "batch": nd},
         "training": {"seconds": t_train, "ms_per_step": t_train / args.train_steps * 1e3, "data_seconds": t_data,
+                     "unrolled": unrolled,
                      "loss_train_val": losses},
     }
     return line
@@ -868,6 +896,8 @@ def main():
     ap.add_argument("--domains", type=int, default=None, help="ensemble: 512; surrogate: 32 held-out domains")
     ap.add_argument("--train-domains", type=int, default=64)
     ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--unroll", type=int, default=4, help="surrogate: windows of the unrolled fine-tuning")
+    ap.add_argument("--unroll-steps", type=int, default=1000, help="surrogate: unrolled fine-tuning steps (0: none)")
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=3e-4)
     ap.add_argument("--max-mass-drift", type=float, default=1e-3)

@@ -157,6 +157,19 @@ int sur_set_norm(sur_model *m, const float *in_mean, const float *in_scale, cons
  * eps 1e-8, bias-corrected).  loss (host, may be NULL) synchronises. */
 int sur_forward_backward(sur_model *m, const float *d_x, const float *d_y, int batch, float *loss);
 int sur_train_step(sur_model *m, const float *d_x, const float *d_y, int batch, float lr, float *loss);
+/* Unrolled training over `windows` = k consecutive windows: the network is applied to
+ * its own prediction, x'_0 = d_x0, x'_{j+1} = x'_j + out_scale * o(x'_j), and
+ *   loss = (1/k) sum_{j=1..k} mean over pixels and channels of ((x'_j - y_j)/out_scale)^2
+ * with the targets y_j = d_targets + (j - 1) * 4 * batch*H*W (planar [k][4][batch*H*W]);
+ * k = 1 is the loss of sur_forward_backward.  Gradients (overwritten) flow through the
+ * whole chain, predictions included.  The predictions are kept (an internal buffer of
+ * (k + 1) * 4 * batch*H*W floats, grown as needed), the activations of one window at a
+ * time: each window's forward pass runs twice.  1 <= k <= 64.  train_step_unrolled adds
+ * the Adam step of sur_train_step.  loss (host, may be NULL) synchronises. */
+int sur_forward_backward_unrolled(sur_model *m, const float *d_x0, const float *d_targets, int windows, int batch,
+                                  float *loss);
+int sur_train_step_unrolled(sur_model *m, const float *d_x0, const float *d_targets, int windows, int batch, float lr,
+                            float *loss);
 /* d_y = x + out_scale * o (d_y may equal d_x). */
 int sur_infer(sur_model *m, const float *d_x, float *d_y, int batch);
 

@@ -62,6 +62,8 @@ struct sur_model {
     int *status;              // [0] tensor-core wait status, [1] non-finite flag
     float *loss;
     double *ind;              // indicators, 2 per domain
+    float *ubuf;              // unrolled training: field gradient and the k predicted states
+    long long ucap;           // floats in ubuf
     int adam_t;
     // Activation arena for `cap` samples.
     int cap;
@@ -454,6 +456,67 @@ int fwd_bwd(sur_model *m, const float *d_x, const float *d_y, int B, float *loss
     return SUR_OK;
 }
 
+// Loss and gradients of `k` windows chained through the network (unrolled training):
+// x'_0 = d_x0, x'_{j+1} = x'_j + out_scale o(x'_j), L = (1/k) sum_j mean ((x'_j - y_j) /
+// out_scale)^2 with the targets y_j = d_targets[j - 1].  The predictions are kept, the
+// activations are not: the backward pass runs j = k .. 1, each time recomputing the
+// forward pass of window j - 1, and carries dL/dx'_j (loss term + identity path + the
+// network path through the first convolution's input gradient) down the chain.
+int fwd_bwd_unrolled(sur_model *m, const float *d_x0, const float *d_targets, int k, int B, float *loss)
+{
+    if (!m || !d_x0 || !d_targets || B < 1 || k < 1 || k > 64) return fail(m, SUR_EINVAL, "invalid arguments");
+    int rc = ensure_batch(m, B, true);
+    if (rc) return rc;
+    const long long M0 = lvl_pix(m, 0, B), F = 4 * M0;
+    const long long need = (long long)(k + 1) * F;
+    if (need > m->ucap) {
+        if (m->ubuf) {
+            CK(cudaStreamSynchronize(m->stream));
+            cudaFree(m->ubuf);
+            m->ubuf = nullptr;
+            m->ucap = 0;
+        }
+        cudaError_t e = cudaMalloc(&m->ubuf, sizeof(float) * need);
+        if (e != cudaSuccess) return fail(m, SUR_ENOMEM, "unrolled buffers of %lld floats: %s", need, cudaGetErrorString(e));
+        m->ucap = need;
+    }
+    float *Gx = m->ubuf;
+    auto state = [&](int j) { return j == 0 ? const_cast<float *>(d_x0) : m->ubuf + (long long)j * F; };
+    CK(cudaMemsetAsync(m->G, 0, sizeof(float) * m->nparam, m->stream));
+    CK(cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream));
+    CK(cudaMemsetAsync(Gx, 0, sizeof(float) * F, m->stream));
+    for (int j = 0; j < k; ++j) {
+        if ((rc = forward(m, state(j), B, false))) return rc;
+        CK(evsur::head(m->Y03, M0, m->lh, m->lw, m->P + m->head_w, m->P + m->head_b, m->norm, state(j), nullptr, 1,
+                       nullptr, nullptr, state(j + 1), m->stream));
+    }
+    const float inv = 1.f / (4.f * (float)M0 * (float)k);
+    for (int j = k; j >= 1; --j) {
+        CK(evsur::unroll_term(state(j), d_targets + (long long)(j - 1) * F, M0, m->norm, inv, Gx, m->dO, m->loss,
+                              m->stream));
+        if ((rc = forward(m, state(j - 1), B, true))) return rc;
+        if ((rc = backward(m, B))) return rc;
+        // backward() leaves the first convolution's dZ in m->dZ.
+        if (j > 1)
+            CK(evsur::conv0_dx(m->dZ, m->conv[0].wb, m->conv[0].kp, M0, m->lh, m->lw, m->norm, Gx, m->stream));
+    }
+    if (loss) {
+        CK(cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+        return check_status(m, nullptr);
+    }
+    return SUR_OK;
+}
+
+// One bias-corrected Adam step on the gradients in m->G, then the BF16 weight copies.
+int adam_update(sur_model *m, float lr)
+{
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    m->adam_t++;
+    const double c1 = 1.0 - pow((double)b1, (double)m->adam_t), c2 = 1.0 - pow((double)b2, (double)m->adam_t);
+    CK(evsur::adam(m->P, m->G, m->Mo, m->Vo, m->nparam, lr, b1, b2, eps, (float)c1, (float)c2, m->stream));
+    return refresh_weights(m);
+}
+
 }  // namespace
 
 extern "C" {
@@ -595,6 +658,7 @@ int sur_free(sur_model *m)
     cudaFree(m->status);
     cudaFree(m->loss);
     cudaFree(m->ind);
+    cudaFree(m->ubuf);
     cudaFree(m->arena);
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;
@@ -657,11 +721,29 @@ int sur_train_step(sur_model *m, const float *d_x, const float *d_y, int batch, 
     if (!m || !(lr >= 0.f)) return fail(m, SUR_EINVAL, "invalid arguments");
     int rc = fwd_bwd(m, d_x, d_y, batch, nullptr);
     if (rc) return rc;
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    m->adam_t++;
-    const double c1 = 1.0 - pow((double)b1, (double)m->adam_t), c2 = 1.0 - pow((double)b2, (double)m->adam_t);
-    CK(evsur::adam(m->P, m->G, m->Mo, m->Vo, m->nparam, lr, b1, b2, eps, (float)c1, (float)c2, m->stream));
-    if ((rc = refresh_weights(m))) return rc;
+    if ((rc = adam_update(m, lr))) return rc;
+    if (loss) {
+        CK(cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+        return check_status(m, nullptr);
+    }
+    return SUR_OK;
+}
+
+int sur_forward_backward_unrolled(sur_model *m, const float *d_x0, const float *d_targets, int windows, int batch,
+                                  float *loss)
+{
+    evtrace::Range trace_("sur_forward_backward_unrolled");
+    return fwd_bwd_unrolled(m, d_x0, d_targets, windows, batch, loss);
+}
+
+int sur_train_step_unrolled(sur_model *m, const float *d_x0, const float *d_targets, int windows, int batch, float lr,
+                            float *loss)
+{
+    evtrace::Range trace_("sur_train_step_unrolled");
+    if (!m || !(lr >= 0.f)) return fail(m, SUR_EINVAL, "invalid arguments");
+    int rc = fwd_bwd_unrolled(m, d_x0, d_targets, windows, batch, nullptr);
+    if (rc) return rc;
+    if ((rc = adam_update(m, lr))) return rc;
     if (loss) {
         CK(cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
         return check_status(m, nullptr);

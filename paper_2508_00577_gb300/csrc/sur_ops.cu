@@ -1,8 +1,9 @@
 // Elementwise and reduction kernels of the learned surrogate on halo-padded
 // NHWC tensors (see surrogate.cuh): SiLU backward, bias gradients, 2x2 average
 // pooling and its adjoint, input packing, the 1x1 head with the loss or the
-// state update, Adam, the BF16 operand copies of the weights, and the
-// per-domain fallback indicators.
+// state update, the loss terms and first-layer input gradient of unrolled
+// training, Adam, the BF16 operand copies of the weights, and the per-domain
+// fallback indicators.
 #include <stdint.h>
 
 #include "surrogate.cuh"
@@ -212,6 +213,78 @@ __global__ void k_head(const bf16 *Y, long long M, int lh, int lw, const float *
 
 // Head backward (C = 32): dY[m][c] = sum_k dO[m][k] Wh[k][c]; dWh[k][c] += sum_m dO[m][k] Y[m][c];
 // dbh[k] += sum_m dO[m][k].  One warp per pixel at a time, lane = channel.
+// Unrolled training (k windows, each applied to the previous prediction): the loss
+// term of a prediction x'_j against its target y_j, r = (x'_j - y_j) / out_scale, added
+// to the planar field gradient G = dL/dx'_j as 2 r / out_scale * inv (inv = 1 / (4 M k)),
+// and the output gradient of the window that produced x'_j, dO = out_scale * G
+// (x'_j = x'_{j-1} + out_scale o).  loss += sum r^2 * inv.
+__global__ void k_unroll_term(const float *xp, const float *yt, long long M, const float *norm, float inv, float *G,
+                              float *dO, float *loss)
+{
+    __shared__ float red[256];
+    float acc = 0.f;
+    GRID_STRIDE(m, M)
+    {
+        float d[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float s = norm[8 + c];
+            const float r = (xp[c * M + m] - yt[c * M + m]) / s;
+            acc += r * r;
+            const float g = G[c * M + m] + 2.f * r / s * inv;
+            G[c * M + m] = g;
+            d[c] = s * g;
+        }
+        *reinterpret_cast<float4 *>(dO + m * 4) = make_float4(d[0], d[1], d[2], d[3]);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0] * inv);
+}
+
+// Input gradient of the first convolution (8 -> 32 channels) in its 4 field channels,
+// dxin[p][c] = sum_tap sum_co W[tap * 8 + c][co] dZ[p - s_tap][co] (s_tap = (dy, dx); the
+// periodic neighbours come from the halo of dZ), added to the planar field gradient:
+// G[c][m] += dxin[m][c] / in_scale[c].  Wb is the forward BF16 copy [32][Kp].
+__global__ void k_conv0_dx(const bf16 *dZ, const bf16 *Wb, int Kp, long long M, int lh, int lw, const float *norm,
+                           float *G)
+{
+    __shared__ float w[9][32][4];
+    for (int e = threadIdx.x; e < 9 * 32 * 4; e += blockDim.x) {
+        const int tap = e / 128, co = (e / 4) % 32, c = e % 4;
+        w[tap][co][c] = __bfloat162float(Wb[co * Kp + tap * 8 + c]);
+    }
+    __syncthreads();
+    const long long Wp = (1 << lw) + 2;
+    GRID_STRIDE(m, M)
+    {
+        const long long p = pad_pix(m, lh, lw);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            const bf16 *z = dZ + (p - dy * Wp - dx) * 32;
+#pragma unroll
+            for (int c8 = 0; c8 < 32; c8 += 8) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(z + c8);
+                const bf16 *h = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float zv = __bfloat162float(h[j]);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[c] += w[tap][c8 + j][c] * zv;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) G[c * M + m] += acc[c] / norm[4 + c];
+    }
+}
+
 __global__ void k_head_bwd(const bf16 *Y, long long M, int lh, int lw, const float *Wh, const float *dO, bf16 *dY,
                            float *dWh, float *dbh)
 {
@@ -402,6 +475,21 @@ cudaError_t head_bwd(const bf16 *Y, long long M, int lh, int lw, const float *Wh
     long long g = (M + 8 * 32 - 1) / (8 * 32);
     if (g > 2048) g = 2048;
     k_head_bwd<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(Y, M, lh, lw, Wh, dO, dY, dWh, dbh);
+    return cudaGetLastError();
+}
+
+cudaError_t unroll_term(const float *xp, const float *yt, long long M, const float *norm, float inv, float *G, float *dO,
+                        float *loss, cudaStream_t st)
+{
+    k_unroll_term<<<grid_1d(M), 256, 0, st>>>(xp, yt, M, norm, inv, G, dO, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t conv0_dx(const bf16 *dZ, const bf16 *Wb, int Kp, long long M, int lh, int lw, const float *norm, float *G,
+                     cudaStream_t st)
+{
+    if (Kp < 72 || (reinterpret_cast<uintptr_t>(dZ) & 15)) return cudaErrorInvalidValue;
+    k_conv0_dx<<<grid_1d(M), 256, 0, st>>>(dZ, Wb, Kp, M, lh, lw, norm, G);
     return cudaGetLastError();
 }
 

@@ -83,6 +83,10 @@ cudaError_t head(const bf16 *Y, long long M, int lh, int lw, const float *Wh, co
                  const float *x, const float *yt, int mode, float *dO, float *loss, float *xn, cudaStream_t st);
 cudaError_t head_bwd(const bf16 *Y, long long M, int lh, int lw, const float *Wh, const float *dO, bf16 *dY,
                      float *dWh, float *dbh, cudaStream_t st);
+cudaError_t unroll_term(const float *xp, const float *yt, long long M, const float *norm, float inv, float *G, float *dO,
+                        float *loss, cudaStream_t st);
+cudaError_t conv0_dx(const bf16 *dZ, const bf16 *Wb, int Kp, long long M, int lh, int lw, const float *norm, float *G,
+                     cudaStream_t st);
 cudaError_t adam(float *w, const float *g, float *m, float *v, long long n, float lr, float b1, float b2, float eps,
                  float c1, float c2, cudaStream_t st);
 cudaError_t conv_weights(const float *Wt, int Cin, int Cout, int Kp, int Kpo, bf16 *Wb, bf16 *Wf, cudaStream_t st);

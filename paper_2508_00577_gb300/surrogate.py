@@ -24,8 +24,8 @@ _ERRNAMES = {SUR_EINVAL: "SUR_EINVAL", SUR_ECUDA: "SUR_ECUDA", SUR_ENOMEM: "SUR_
 # Every symbol include/evsur.h declares.
 EXPORTED_SYMBOLS = (
     "sur_gemm", "sur_set_tma", "sur_init", "sur_free", "sur_num_params", "sur_get_params", "sur_set_params", "sur_get_grads",
-    "sur_set_norm", "sur_forward_backward", "sur_train_step", "sur_infer", "sur_indicators", "sur_rollout",
-    "sur_last_error",
+    "sur_set_norm", "sur_forward_backward", "sur_train_step", "sur_forward_backward_unrolled",
+    "sur_train_step_unrolled", "sur_infer", "sur_indicators", "sur_rollout", "sur_last_error",
 )
 
 # Architecture tables (same as the C runtime): 3x3 convolutions (Cin, Cout) in
@@ -82,6 +82,8 @@ def lib():
             L.sur_set_norm.argtypes = [vp, fp, fp, fp]
             L.sur_forward_backward.argtypes = [vp, vp, vp, ip, fp]
             L.sur_train_step.argtypes = [vp, vp, vp, ip, ctypes.c_float, fp]
+            L.sur_forward_backward_unrolled.argtypes = [vp, vp, vp, ip, ip, fp]
+            L.sur_train_step_unrolled.argtypes = [vp, vp, vp, ip, ip, ctypes.c_float, fp]
             L.sur_infer.argtypes = [vp, vp, vp, ip]
             L.sur_indicators.argtypes = [vp, ip, ip, ip, ctypes.c_float, vp, vp]
             L.sur_rollout.argtypes = [vp, vp, vp, ip, ctypes.POINTER(sur_rollout_cfg),
@@ -159,6 +161,20 @@ def sur_train_step(model, d_x, d_y, batch, lr, want_loss=True):
     return loss.value if want_loss else None
 
 
+def sur_forward_backward_unrolled(model, d_x0, d_targets, windows, batch, want_loss=True):
+    loss = ctypes.c_float(0.0)
+    _check(lib().sur_forward_backward_unrolled(model, d_x0, d_targets, windows, batch,
+                                               ctypes.byref(loss) if want_loss else None), model)
+    return loss.value if want_loss else None
+
+
+def sur_train_step_unrolled(model, d_x0, d_targets, windows, batch, lr, want_loss=True):
+    loss = ctypes.c_float(0.0)
+    _check(lib().sur_train_step_unrolled(model, d_x0, d_targets, windows, batch, lr,
+                                         ctypes.byref(loss) if want_loss else None), model)
+    return loss.value if want_loss else None
+
+
 def sur_infer(model, d_x, d_y, batch):
     _check(lib().sur_infer(model, d_x, d_y, batch), model)
 
@@ -231,6 +247,12 @@ class Surrogate:
 
     def train_step(self, d_x, d_y, batch, lr, want_loss=True):
         return sur_train_step(self.m, d_x, d_y, batch, lr, want_loss)
+
+    def forward_backward_unrolled(self, d_x0, d_targets, windows, batch):
+        return sur_forward_backward_unrolled(self.m, d_x0, d_targets, windows, batch)
+
+    def train_step_unrolled(self, d_x0, d_targets, windows, batch, lr, want_loss=True):
+        return sur_train_step_unrolled(self.m, d_x0, d_targets, windows, batch, lr, want_loss)
 
     def infer(self, d_x, d_y, batch):
         sur_infer(self.m, d_x, d_y, batch)

@@ -314,6 +314,56 @@ def test_network_forward_backward_against_oracle(tma):
     assert inc_err <= 2e-2
 
 
+@pytest.mark.parametrize("k", [1, 3])
+def test_unrolled_forward_backward_against_oracle(k):
+    """k windows chained through the network (sur_forward_backward_unrolled): loss and every
+    gradient tensor against the oracle's unrolled_loss_and_grad with the same BF16-rounded
+    weights (tolerances of the single-window test); k = 1 also against the window loss."""
+    Bn, H, W = 2, 16, 32
+    x, _ = smooth_fields(Bn, H, W, 4)
+    base = (x - NORM[0][:, None]) / NORM[1][:, None]
+    targets = np.stack([x + (j + 1) * 0.5 * NORM[2][:, None] * np.roll(base, j + 1, axis=1) for j in range(k)])
+    with S.Surrogate(H, W, seed=6) as m:
+        m.set_norm(*NORM)
+        theta = m.params()
+        layout, n = S.param_layout()
+        off = dict((nm, (o, s)) for nm, o, s in layout)
+        o, s = off["head.w"]
+        theta[o:o + 4 * S.BASE] *= 10.0
+        m.set_params(theta)
+        dx = torch.tensor(x, dtype=torch.float32, device=dev).contiguous()
+        dt = torch.tensor(targets.reshape(k * 4, -1), dtype=torch.float32, device=dev).contiguous()
+        torch.cuda.synchronize()
+        loss = m.forward_backward_unrolled(dx.data_ptr(), dt.data_ptr(), k, Bn)
+        g_gpu = m.grads().astype(np.float64)
+        if k == 1:
+            loss1 = m.forward_backward(dx.data_ptr(), dt.data_ptr(), Bn)
+            g1 = m.grads().astype(np.float64)
+            assert abs(loss - loss1) <= 1e-4 * loss1
+            assert rel_l2(g_gpu, g1) <= 1e-3
+    theta_b = theta.astype(np.float64).copy()
+    for nm, o, shp in layout:
+        if nm.endswith(".w") and not nm.startswith("head"):
+            sz = int(np.prod(shp))
+            theta_b[o:o + sz] = bf16_round(theta_b[o:o + sz])
+    P = U.unpack(theta_b)
+    x32 = x.astype(np.float32).astype(np.float64)
+    t32 = targets.astype(np.float32).astype(np.float64)
+    loss_o, G, _ = U.unrolled_loss_and_grad(P, x32, list(t32), Bn, H, W, NORM)
+    assert abs(loss - loss_o) <= 2e-2 * loss_o, (loss, loss_o)
+    g_orc = U.pack(G, n)
+    report = []
+    for nm, o, shp in layout:
+        sz = int(np.prod(shp))
+        a, b = g_gpu[o:o + sz], g_orc[o:o + sz]
+        assert np.all(np.isfinite(a)), nm
+        e = rel_l2(a, b)
+        report.append((nm, e))
+        assert e <= 6e-2, (nm, e)
+    print(f"\nk = {k}: loss {loss:.5e} (oracle {loss_o:.5e}); worst gradient tensors:",
+          sorted(report, key=lambda t: -t[1])[:3])
+
+
 def test_training_reduces_loss():
     Bn, H, W = 4, 32, 32
     x, y = smooth_fields(Bn, H, W, 9)
