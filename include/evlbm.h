@@ -223,8 +223,8 @@ int lbm_set_tile(lbm_ctx *ctx, int tile_w, int tile_h);
 int lbm_get_tile(const lbm_ctx *ctx, int *tile_w, int *tile_h);
 
 /* Autotuner: times every candidate launch shape of the fused kernel for
- * probe_steps (>= 1) steps each with CUDA events on the context's stream and
- * keeps the fastest.  The probes read the current state and write the spare
+ * probe_steps (>= 1) steps each with CUDA events on the context's stream, in two
+ * rounds over all candidates, and keeps the shape with the fastest time.  The probes read the current state and write the spare
  * buffer, so the state is unchanged.  Synchronises the stream.  The chosen shape
  * is returned in *tile_w, *tile_h (either may be NULL); both are 0 when the
  * context has no fused kernel.  Errors: LBM_EINVAL, LBM_ECUDA. */

@@ -448,6 +448,9 @@ int lbm_get_tile(const lbm_ctx *c, int *tile_w, int *tile_h)
 
 // z-chunk height of the fused D3Q27 kernel by timed probes on the live state
 // (its output buffer is the spare one, so the state is unchanged).
+// Rounds of the autotuners' candidate sweep (each candidate keeps its fastest round).
+constexpr int kAutotuneRounds = 2;
+
 static int autotune3d(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
 {
     cudaEvent_t e0, e1;
@@ -455,10 +458,12 @@ static int autotune3d(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
     CK(c, cudaEventCreate(&e1));
     const int heights[] = {8, 16, 32, 64, 128, 256};
     const int nx = c->cur ^ 1;
-    float best = 1e30f;
-    int bh = 0;
+    float tmin[6] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
     KParams K = c->K;
     cudaError_t e = cudaSuccess;
+    // Two rounds over the candidates, each keeping its faster time: a single probe of a
+    // few launches is not repeatable to the few per cent that separate neighbouring chunks.
+    for (int round = 0; round < kAutotuneRounds; ++round)
     for (int hi = 0; hi < 6 && e == cudaSuccess; ++hi) {
         const int H = heights[hi] < c->P.nz ? heights[hi] : c->P.nz;
         if (hi > 0 && H == (heights[hi - 1] < c->P.nz ? heights[hi - 1] : c->P.nz)) continue;
@@ -474,14 +479,18 @@ static int autotune3d(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e == cudaSuccess && ms < best) {
-            best = ms;
-            bh = H;
-        }
+        if (e == cudaSuccess && ms < tmin[hi]) tmin[hi] = ms;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_autotune");
+    int bh = 0;
+    float best = 1e30f;
+    for (int hi = 0; hi < 6; ++hi)
+        if (tmin[hi] < best) {
+            best = tmin[hi];
+            bh = heights[hi] < c->P.nz ? heights[hi] : c->P.nz;
+        }
     c->K.tile_w = evlbm::kFused3dTile;
     c->K.tile_h = bh;
     if (tile_w) *tile_w = evlbm::kFused3dTile;
@@ -501,10 +510,10 @@ int lbm_autotune(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
     CK(c, cudaEventCreate(&e1));
     const int heights[] = {16, 32, 64, 128, 256, LBM_TILE_BALANCED};
     const int nx = c->cur ^ 1;
-    float best = 1e30f;
-    int bw = 0, bh = 0;
+    std::vector<float> tmin(evlbm::kFusedWidthCount * 6, 1e30f);
     KParams K = c->K;
     cudaError_t e = cudaSuccess;
+    for (int round = 0; round < kAutotuneRounds; ++round)
     for (int wi = 0; wi < evlbm::kFusedWidthCount && e == cudaSuccess; ++wi) {
         const int W = evlbm::kFusedWidths[wi];
         if (W > 2 * c->P.nx && W != evlbm::kFusedWidths[0]) continue;
@@ -524,16 +533,21 @@ int lbm_autotune(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e == cudaSuccess && ms < best) {
-                best = ms;
-                bw = W;
-                bh = H;
-            }
+            if (e == cudaSuccess && ms < tmin[wi * 6 + hi]) tmin[wi * 6 + hi] = ms;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_autotune");
+    int bw = 0, bh = 0;
+    float best = 1e30f;
+    for (int wi = 0; wi < evlbm::kFusedWidthCount; ++wi)
+        for (int hi = 0; hi < 6; ++hi)
+            if (tmin[wi * 6 + hi] < best) {
+                best = tmin[wi * 6 + hi];
+                bw = evlbm::kFusedWidths[wi];
+                bh = heights[hi] < c->P.ny ? heights[hi] : c->P.ny;
+            }
     c->K.tile_w = bw;
     c->K.tile_h = bh;
     if (tile_w) *tile_w = bw;
