@@ -17,7 +17,8 @@
 //   C: F, u, T, EOS (q-2)          stress of q-3..q-1, pulled g   (18 x 18)
 //   D: collide (q-3)               u, T fields of q-4..q-2, the tile's pulled f from
 //                                  the TMEM stash stage A wrote 3 planes ago, pulled g
-//                                  again (L2 hits: stage C read them 1 plane ago)
+//                                  again (L2 hits: stage C read them 1 plane ago; FP32
+//                                  loads them at the start of stage C)
 // Shared fields live in 3-deep plane rings sized to the region that reads them;
 // centre values pass from C to D through a one-plane per-thread slot (stage C takes
 // the tile column a thread collides in D first, and reads the slot before rewriting
@@ -294,8 +295,11 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
         }
         __syncthreads();
 
+        const bool haveP = q - 1 >= z0 - 2 && q - 1 <= zend + 1;   // stage B writes Pi(q-1)
+        const bool runC = q - 2 >= z0 - 1 && q - 2 <= zend;        // stage C's plane is needed
+
         // ---------------- B: Korteweg stress of plane q-1 ----------------
-        if (q - 1 >= z0 - 2 && q - 1 <= zend + 1) {
+        if (haveP) {
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 int cx, cy;
@@ -337,12 +341,24 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
         // into the partial forces of planes q (first term), q-1 and q-2 (complete), kept
         // per stage-C column (thread-private).
         float cprev[7];                                   // centre values of plane q-3 (stage D)
-        const bool haveP = q - 1 >= z0 - 2 && q - 1 <= zend + 1;   // stage B wrote Pi(q-1)
+        // Software pipelining (FP32 thermal): stage D's pulled g (plane q-3) are loaded at the
+        // start of stage C, so that their latency overlaps stage C and its barrier instead
+        // of following it.  (Loading stage C's g before stage B the same way made the kernel
+        // 11 % slower.)
+        constexpr bool PRE = THERMAL && !DEV;
+        float gD[27];
+        if constexpr (PRE) {
+            if (q - 3 >= z0 && q - 3 < zend) {
+                unsigned zo[3];
+                plane_offsets(q - 3, nx, ny, nz, zo);
+#pragma unroll
+                for (int i = 0; i < 27; ++i) gD[i] = ldc(A.g, src_of(i, cD, zo, N), 27ull * N);
+            }
+        }
         if (haveP) {
             unsigned zo[3];
             if (THERMAL) plane_offsets(q - 2, nx, ny, nz, zo);
             const int zc = wrapi(q - 2, nz);
-            const bool runC = q - 2 >= z0 - 1 && q - 2 <= zend;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 int cx, cy;
@@ -628,7 +644,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
                             const int cx = j % 3 - 1, cy = j / 3 - 1;
                             const unsigned sn = zs + cD.yo[1 - cy] + cD.xo[1 - cx];
                             const unsigned i = (unsigned)j + 9u * (unsigned)kz;
-                            const float h = ldc(A.g, i * N + sn, 27ull * N);       // FP32 storage here
+                            const float h = PRE ? gD[i] : ldc(A.g, i * N + sn, 27ull * N);   // FP32 storage here
                             const float geq = ref_g_of(Ag[cx + 1], rex[cx + 1], E[cy + 1], C[cy + 1]);
                             float gst = As[cx + 1] * P[cy + 1] + rpx[cx + 1] * Dd[cy + 1];
                             // g' on the |c| = 1 populations
