@@ -334,7 +334,8 @@ int lbm_batch_moments(lbm_batch *b, int domain, double *rho, double *u, double *
 int lbm_batch_set_tile(lbm_batch *b, int tile_w, int tile_h);
 int lbm_batch_get_tile(const lbm_batch *b, int *tile_w, int *tile_h);
 
-/* Autotuner: times every launch shape on one persistent launch of 2 * probe_steps
+/* Autotuner: times every launch shape (strip widths 64, 96, 128, 192 x chunk heights
+ * 32, 64, 128, 256, 512) on one persistent launch of 2 * probe_steps
  * steps from a device copy of the current state (steps overlap inside a launch as
  * in a run), restoring the state before each probe and at the end; keeps the
  * fastest.  The copy takes as much device memory as the populations of one buffer

@@ -571,7 +571,7 @@ int lbm_batch_get_tile(const lbm_batch *b, int *tile_w, int *tile_h)
 int lbm_batch_autotune(lbm_batch *b, int probe_steps, int *tile_w, int *tile_h)
 {
     if (!b || probe_steps < 1) return LBM_EINVAL;
-    const int heights[] = {32, 64, 128, 256};
+    const int heights[] = {32, 64, 128, 256, 512};     // 512: every domain of <= 512 rows in one chunk
     // Each shape is timed on one persistent launch of 2 * probe_steps steps, as in a run,
     // where the last items of a step overlap the first items of the next.  The launch
     // starts from a copy of the current state; an even step count ends in the current
@@ -605,7 +605,7 @@ int lbm_batch_autotune(lbm_batch *b, int probe_steps, int *tile_w, int *tile_h)
     const bool have_copy = saved && copy_state(false) == cudaSuccess;
     if (saved && !have_copy) rc = LBM_ECUDA;
     for (int wi = 0; wi < evlbm::kFusedWidthCount && rc == LBM_OK; ++wi) {
-        for (int hi = 0; hi < 4 && rc == LBM_OK; ++hi) {
+        for (int hi = 0; hi < 5 && rc == LBM_OK; ++hi) {
             b->tile_w = evlbm::kFusedWidths[wi];
             b->tile_h = heights[hi];
             if ((rc = retile(b))) break;
