@@ -668,9 +668,9 @@ def run_spinodal3d(args):
                                tau=TAU, precision=prec)
         stream = torch.cuda.Stream()
         with ev.Lattice(p, rho, u, T, stream=stream.cuda_stream) as g:
-            if args.tile:                            # fixed 16 x H (z-chunk) launch shape
-                tile = tuple(int(v) for v in args.tile.split(","))
-                ev.lbm_set_tile(g.ctx, *tile)
+            if args.tile:                            # fixed z-chunk H (--tile W,H: W is the kernel's own)
+                ev.lbm_set_tile(g.ctx, 0, int(args.tile.split(",")[-1]))
+                tile = ev.lbm_get_tile(g.ctx)
             else:
                 tile = ev.lbm_autotune(g.ctx, 2)     # z-chunk of the fused kernel
             g.step(args.warmup)

@@ -207,8 +207,10 @@ int lbm_launches_per_step(const lbm_ctx *ctx);
  * Errors: LBM_EINVAL. */
 int lbm_set_walls(lbm_ctx *ctx, int enable, const double u_lo[3], const double u_hi[3], double T_w);
 
-/* Launch shape of the fused single-pass kernels.  D3Q27: tile_w = 16
- * (16 x 16 columns per CTA) and tile_h = the z-chunk a CTA marches through (>= 1).
+/* Launch shape of the fused single-pass kernels.  D3Q27: tile_w = 0 or the kernel's
+ * fixed tile width for the storage type (32: tiles of 32 x 8 columns per CTA for FP32;
+ * 16: 16 x 16 for FP16/BF16 storage; lbm_get_tile reports it) and tile_h = the z-chunk a
+ * CTA marches through (>= 1).
  * D2Q9: strips of
  * tile_w columns (one of 64, 96, 128, 192) marching over chunks of tile_h rows
  * (>= 1; rounded up to an even number, the kernel advances two rows at a time), or

@@ -424,8 +424,10 @@ int lbm_set_tile(lbm_ctx *c, int tile_w, int tile_h)
     if (!c) return LBM_EINVAL;
     bool ok = tile_w == 0 && tile_h == 0;
     if (c->Q == 27) {
-        ok = ok || (tile_w == evlbm::kFused3dTile && tile_h >= 1);
-        if (!ok) return fail(c, LBM_EINVAL, "D3Q27: tile_w must be 16 and tile_h (z-chunk) >= 1 (or both 0)");
+        ok = ok || ((tile_w == 0 || tile_w == evlbm::fused3d_tile_w(c->P.precision)) && tile_h >= 1);
+        if (!ok)
+            return fail(c, LBM_EINVAL, "D3Q27: tile_w must be 0 or the kernel's tile width (%d) and tile_h (z-chunk) >= 1",
+                        evlbm::fused3d_tile_w(c->P.precision));
     } else {
         for (int k = 0; k < evlbm::kFusedWidthCount; ++k)
             ok = ok || (tile_w == evlbm::kFusedWidths[k] && (tile_h >= 1 || tile_h == LBM_TILE_BALANCED));
@@ -433,7 +435,7 @@ int lbm_set_tile(lbm_ctx *c, int tile_w, int tile_h)
             return fail(c, LBM_EINVAL,
                         "tile_w must be one of 64,96,128,192 and tile_h >= 1 or LBM_TILE_BALANCED (or both 0)");
     }
-    c->K.tile_w = tile_w;
+    c->K.tile_w = (c->Q == 27 && tile_h >= 1) ? evlbm::fused3d_tile_w(c->P.precision) : tile_w;
     c->K.tile_h = tile_h;
     return LBM_OK;
 }
@@ -467,7 +469,7 @@ static int autotune3d(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
     for (int hi = 0; hi < 6 && e == cudaSuccess; ++hi) {
         const int H = heights[hi] < c->P.nz ? heights[hi] : c->P.nz;
         if (hi > 0 && H == (heights[hi - 1] < c->P.nz ? heights[hi - 1] : c->P.nz)) continue;
-        K.tile_w = evlbm::kFused3dTile;
+        K.tile_w = evlbm::fused3d_tile_w(c->P.precision);
         K.tile_h = H;
         for (int s = 0; s <= probe_steps && e == cudaSuccess; ++s) {
             if (s == 1) e = cudaEventRecord(e0, c->stream);
@@ -491,9 +493,9 @@ static int autotune3d(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
             best = tmin[hi];
             bh = heights[hi] < c->P.nz ? heights[hi] : c->P.nz;
         }
-    c->K.tile_w = evlbm::kFused3dTile;
+    c->K.tile_w = evlbm::fused3d_tile_w(c->P.precision);
     c->K.tile_h = bh;
-    if (tile_w) *tile_w = evlbm::kFused3dTile;
+    if (tile_w) *tile_w = evlbm::fused3d_tile_w(c->P.precision);
     if (tile_h) *tile_h = bh;
     return LBM_OK;
 }

@@ -50,9 +50,10 @@ extern const int kFusedWidths[kFusedWidthCount];
 void fused2d_default_tile(const KParams &p, int *W, int *H);
 bool fused2d_supported(int prec, int Q, const KParams &p);
 // Fused single-pass D3Q27 step (FP32 arithmetic, divergence force form; storage prec
-// 1/2/3 as above, 16-bit storage reading Rin and writing Rout); the x-y tile is
-// kFused3dTile x kFused3dTile columns, tile_h is the z-chunk height (0 = default).
-constexpr int kFused3dTile = 16;
+// 1/2/3 as above, 16-bit storage reading Rin and writing Rout); the x-y tile of 256
+// columns is fused3d_tile_w(prec) wide (32 x 8 for FP32, 16 x 16 for 16-bit storage),
+// tile_h is the z-chunk height (0 = default).
+int fused3d_tile_w(int prec);
 bool fused3d_supported(int prec, int Q, const KParams &p);
 cudaError_t fused3d_step(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
                          const void *RT_iso, const void *Rin, void *Rout, cudaStream_t st);

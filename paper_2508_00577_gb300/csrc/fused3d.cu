@@ -7,14 +7,15 @@
 // Phi, Phi', q' (Eqs. correction_u/gamma/q), the equilibria (Eqs. feq, f_star,
 // geq, gstar, g_corr) and the collision of Eq. (pre_LBM).
 //
-// Work decomposition (2.5-D z-marching).  A CTA owns a 16 x 16 tile of (x, y)
-// output columns of one z-chunk and walks its planes one per iteration; four
+// Work decomposition (2.5-D z-marching).  A CTA owns a tile of 256 (x, y) output columns
+// (32 x 8 with FP32 storage, 16 x 16 with 16-bit storage, see TileOf) of one z-chunk and
+// walks its planes one per iteration; four
 // stages lag by one plane because the collision needs u and T within radius 1,
 // hence F within radius 1, hence the Korteweg stress within radius 2, hence rho
 // within radius 3:
-//   A: rho, j (plane q)            pulled f           on the tile + 3 halo columns (22 x 22)
-//   B: Korteweg stress (q-1)       rho of q-2..q      on the tile + 2 (20 x 20)
-//   C: F, u, T, EOS (q-2)          stress of q-3..q-1, pulled g   (18 x 18)
+//   A: rho, j (plane q)            pulled f           on the tile + 3 halo columns
+//   B: Korteweg stress (q-1)       rho of q-2..q      on the tile + 2
+//   C: F, u, T, EOS (q-2)          stress of q-3..q-1, pulled g   on the tile + 1
 //   D: collide (q-3)               u, T fields of q-4..q-2, the tile's pulled f from
 //                                  the TMEM stash stage A wrote 3 planes ago, pulled g
 //                                  again (L2 hits: stage C read them 1 plane ago; FP32
@@ -22,7 +23,7 @@
 // Shared fields live in 3-deep plane rings sized to the region that reads them;
 // centre values pass from C to D through a one-plane per-thread slot (stage C takes
 // the tile column a thread collides in D first, and reads the slot before rewriting
-// it); at 73.1 KB per CTA two CTAs leave the L1 ~92 KB for loads in flight.
+// it); at 73-77 KB per CTA two CTAs leave the L1 ~85 KB for loads in flight.
 //
 // 16-bit storage: every pulled population is rebuilt from its source node's FP32
 // reference record (a 16- and an 8-byte load, L1/L2 hits after the first) and the
@@ -37,19 +38,33 @@ namespace evlbm {
 
 namespace {
 
-constexpr int TX = 16, TY = 16, NT = TX * TY;     // output columns per CTA, threads per CTA
-constexpr int WA = TX + 6, WB = TX + 4, WC = TX + 2;
-constexpr int SA = WA * WA, SB = WB * WB, SC = WC * WC;
+constexpr int NT = 256;                           // threads per CTA, one output column each
 
-// Shared-memory layout (floats).
-constexpr int O_RHO = 0;                          // [3][SA]
-constexpr int O_J = O_RHO + 3 * SA;               // [3 planes][3 comps][SC]
-constexpr int O_PI = O_J + 9 * SC;                // [6 comps][SB]  xx xy xz yy yz zz of the newest plane
-constexpr int O_PF = O_PI + 6 * SB;               // [3 planes][3 comps][SC]  partial forces, per stage-C column
-constexpr int O_CF = O_PF + 9 * SC;               // [3 planes][7][SC]  ux uy uz qx qy qz wq
-constexpr int O_CEN = O_CF + 21 * SC;             // [7][NT]  rho Fx Fy Fz RT theta0 gamma0 (one plane)
-constexpr int SMEM_FLOATS = O_CEN + 7 * NT;
-constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
+// Geometry of a TX x TY tile (TX TY = NT): region widths (x, the row stride) and sizes of
+// the tile + 3 / + 2 / + 1 halo regions of stages A / B / C, and the shared-memory layout.
+template <int TX_, int TY_> struct Geo {
+    static constexpr int TX = TX_, TY = TY_;
+    static_assert(TX * TY == NT, "one thread per output column");
+    static constexpr int WA = TX + 6, WB = TX + 4, WC = TX + 2;
+    static constexpr int SA = WA * (TY + 6), SB = WB * (TY + 4), SC = WC * (TY + 2);
+    // Column passes of stages A and B (NT columns per pass); stage C's ring fits in one.
+    static constexpr int PA = (SA + NT - 1) / NT, PB = (SB + NT - 1) / NT;
+    static_assert(2 * WC + 2 * TY <= NT, "stage C's ring columns exceed one pass");
+    // Shared-memory layout (floats).
+    static constexpr int O_RHO = 0;               // [3][SA]
+    static constexpr int O_J = O_RHO + 3 * SA;    // [3 planes][3 comps][SC]
+    static constexpr int O_PI = O_J + 9 * SC;     // [6 comps][SB]  xx xy xz yy yz zz of the newest plane
+    static constexpr int O_PF = O_PI + 6 * SB;    // [3 planes][3 comps][SC]  partial forces, per stage-C column
+    static constexpr int O_CF = O_PF + 9 * SC;    // [3 planes][7][SC]  ux uy uz qx qy qz wq
+    static constexpr int O_CEN = O_CF + 21 * SC;  // [7][NT]  rho Fx Fy Fz RT theta0 gamma0 (one plane)
+    static constexpr size_t SMEM_BYTES = sizeof(float) * (O_CEN + 7 * NT);
+};
+// Tile shape per storage type.  FP32: 32 x 8, so that a warp's load of one population is
+// one row of 32 consecutive nodes (16 x 16 tiles load two half rows per warp; 32 x 8 ran
+// 7 % faster despite 10 % more halo columns).  16-bit storage: 16 x 16, whose smaller halo
+// saves more decoding than the wider rows save in loads (32 x 8 was 3.5 % slower).
+template <typename S> struct TileOf { using G = Geo<16, 16>; };
+template <> struct TileOf<float> { using G = Geo<32, 8>; };
 
 template <typename S> struct Args {
     const S *f, *g;
@@ -209,6 +224,9 @@ template <bool THERMAL, typename S>
 __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
 {
     constexpr bool DEV = Store<S>::dev;
+    using G = typename TileOf<S>::G;
+    constexpr int TX = G::TX, TY = G::TY, WA = G::WA, WB = G::WB, WC = G::WC;
+    constexpr int SA = G::SA, SB = G::SB, SC = G::SC, PA = G::PA, PB = G::PB;
     extern __shared__ float sm[];
     const int t = threadIdx.x;
     const int nx = A.nx, ny = A.ny, nz = A.nz;
@@ -219,11 +237,11 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
 
     // Columns this thread handles in stages A, B, C (up to two each).
     // Stage A: first the thread's own tile column (whose pulled f it stashes for stage D),
-    // then the 228 halo columns on threads 0..227: three rows above and below the tile
-    // (22 columns each), then three columns left and right of each tile row.
+    // then the halo columns, NT per further pass: three rows above and below the tile
+    // (WA columns each), then three columns left and right of each tile row.
     auto colA = [&](int k, int &cx, int &cy) {
         if (k == 0) { cx = t % TX; cy = t / TX; return true; }
-        const int r = t;
+        const int r = t + (k - 1) * NT;
         if (r < 3 * WA) { cx = r % WA - 3; cy = r / WA - 3; }
         else if (r < 6 * WA) { cx = (r - 3 * WA) % WA - 3; cy = TY + (r - 3 * WA) / WA; }
         else { const int m = (r - 6 * WA) % 6; cy = (r - 6 * WA) / 6; cx = m < 3 ? m - 3 : TX + m - 3; }
@@ -244,7 +262,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
     auto sa = [](int cx, int cy) { return (cy + 3) * WA + (cx + 3); };
     auto sb = [](int cx, int cy) { return (cy + 2) * WB + (cx + 2); };
     auto sc = [](int cx, int cy) { return (cy + 1) * WC + (cx + 1); };
-    float *RHO = sm + O_RHO, *J = sm + O_J, *PI = sm + O_PI, *PF = sm + O_PF, *CF = sm + O_CF, *CEN = sm + O_CEN;
+    float *RHO = sm + G::O_RHO, *J = sm + G::O_J, *PI = sm + G::O_PI, *PF = sm + G::O_PF, *CF = sm + G::O_CF,
+          *CEN = sm + G::O_CEN;
 
     const int dcx = t % TX, dcy = t / TX;                 // this thread's output column
     const bool inD = x0 + dcx < nx && y0 + dcy < ny;
@@ -266,7 +285,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
             unsigned zo[3];
             plane_offsets(q, nx, ny, nz, zo);
 #pragma unroll 1
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < PA; ++k) {
                 int cx, cy;
                 if (!colA(k, cx, cy)) continue;
                 const Cell c = cell_of(x0 + cx, y0 + cy, nx, ny);
@@ -301,7 +320,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
         // ---------------- B: Korteweg stress of plane q-1 ----------------
         if (haveP) {
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < PB; ++k) {
                 int cx, cy;
                 if (!colB(k, cx, cy)) continue;
                 const float *r[3] = {RHO + sm2 * SA, RHO + sm1 * SA, RHO + s0 * SA};   // planes q-2, q-1, q
@@ -665,17 +684,18 @@ __global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
 template <bool THERMAL, typename S>
 cudaError_t launch(const Args<S> &A, cudaStream_t st)
 {
+    using G = typename TileOf<S>::G;
     static int attr_dev = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (attr_dev != dev) {
-        e = cudaFuncSetAttribute(k_fused3d<THERMAL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        e = cudaFuncSetAttribute(k_fused3d<THERMAL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    const dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY, (A.nz + A.HZ - 1) / A.HZ);
-    k_fused3d<THERMAL, S><<<grid, NT, SMEM_BYTES, st>>>(A);
+    const dim3 grid((A.nx + G::TX - 1) / G::TX, (A.ny + G::TY - 1) / G::TY, (A.nz + A.HZ - 1) / A.HZ);
+    k_fused3d<THERMAL, S><<<grid, NT, G::SMEM_BYTES, st>>>(A);
     return cudaGetLastError();
 }
 
@@ -709,6 +729,11 @@ cudaError_t step_t(const KParams &p, const void *f, const void *g, void *fo, voi
 }  // namespace
 
 EVLBM_DEFINE_OOB_READER(fused3d_oob)
+
+int fused3d_tile_w(int prec)
+{
+    return prec == 1 ? TileOf<float>::G::TX : TileOf<__half>::G::TX;
+}
 
 bool fused3d_supported(int prec, int Q, const KParams &p)
 {

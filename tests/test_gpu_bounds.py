@@ -50,7 +50,7 @@ for (nx, ny, nz, hz) in [(20, 18, 11, 4), (33, 16, 7, 3), (5, 3, 4, 1), (17, 17,
     p = ev.lbm_params.make(lattice=ev.LBM_D3Q27, nx=nx, ny=ny, nz=nz, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=kappa,
                            precision=ev.LBM_FP32)
     with ev.Lattice(p, *f) as g:
-        ev.lbm_set_tile(g.ctx, 16, hz)
+        ev.lbm_set_tile(g.ctx, 0, hz)
         g.step(4)
         rho = g.moments()[0]
     o = oracle.State(oracle.Params(Q=27, nx=nx, ny=ny, nz=nz, eos=E.CS, a=A, b=B, kappa=kappa, tau=0.3), *f)
@@ -62,7 +62,7 @@ for (nx, ny, nz, hz) in [(20, 18, 11, 4), (33, 16, 7, 3), (5, 3, 4, 1), (17, 17,
             p16 = ev.lbm_params.make(lattice=ev.LBM_D3Q27, nx=nx, ny=ny, nz=nz, eos=ev.LBM_EOS_CS, a=A, b=B,
                                      kappa=kappa, precision=prec)
             with ev.Lattice(p16, *f) as g:
-                ev.lbm_set_tile(g.ctx, 16, hz)
+                ev.lbm_set_tile(g.ctx, 0, hz)
                 g.step(4)
                 check(f"d3q27 {tag} {nx}x{ny}x{nz} z-chunk {hz}", o, g.moments()[0])
 # Wall columns of the fused D2Q9 kernel (thermal Couette set-up, kappa = 0), ragged strip.

@@ -168,8 +168,8 @@ def test_fp32_d2q9(nx, ny, nz):
                                          (40, 35, 9, 3)])
 def test_fp32_d3q27(nx, ny, nz, hz, thermal):
     """FP32 D3Q27 (fused single-pass kernel): max |d rho|/rho <= 1e-5 over 10 steps of a
-    spinodal state with 5 % density noise.  Edges that are not multiples of the 16 x 16
-    tile, odd plane counts, z-chunks that do not divide nz (hz; 0 = default chunk) and a
+    spinodal state with 5 % density noise.  Edges that are not multiples of the 32 x 8
+    tile (16 x 16 with 16-bit storage), odd plane counts, z-chunks that do not divide nz (hz; 0 = default chunk) and a
     lattice smaller than one tile."""
     _, Tc = E.critical_point(E.CS, A, B)
     RT = 0.85 * Tc
@@ -179,7 +179,7 @@ def test_fp32_d3q27(nx, ny, nz, hz, thermal):
     o, g = pair(27, nx, ny, nz, fields, kappa, ev.LBM_FP32, thermal=thermal)
     with g:
         if hz:
-            ev.lbm_set_tile(g.ctx, 16, hz)
+            ev.lbm_set_tile(g.ctx, 0, hz)
         assert ev.lbm_launches_per_step(g.ctx) == 1       # the fused kernel, not the stage kernels
         o.step(10)
         g.step(10)
@@ -372,3 +372,30 @@ def test_autotune_keeps_state():
             ev.lbm_set_tile(g.ctx, 100, 10)
         with pytest.raises(ev.LBMError):
             ev.lbm_set_tile(g.ctx, 128, -2)
+
+
+@pytest.mark.parametrize("prec,width", [(ev.LBM_FP32, 32), (ev.LBM_FP16_DEV, 16), (ev.LBM_BF16_DEV, 16)])
+def test_d3q27_tile_shape_per_storage(prec, width):
+    """The D3Q27 kernel's x-y tile is fixed per storage type (32 x 8 for FP32, 16 x 16
+    for 16-bit storage): lbm_set_tile takes tile_w = 0 or that width, lbm_get_tile and
+    lbm_autotune report it, and the autotuner leaves the state as it was."""
+    _, Tc = E.critical_point(E.CS, A, B)
+    RT = 0.85 * Tc
+    s1, s2 = E.spinodal(E.CS, A, B, RT)
+    kappa = E.kappa_for_width(E.CS, A, B, RT, 4.0)
+    f = inputs.spinodal_noise(40, 24, 12, 0.5 * (s1 + s2), RT, amplitude=0.05, D=3)
+    p = ev.lbm_params.make(lattice=ev.LBM_D3Q27, nx=40, ny=24, nz=12, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=kappa,
+                           precision=prec)
+    with ev.Lattice(p, *f) as g:
+        ev.lbm_set_tile(g.ctx, 0, 5)
+        assert ev.lbm_get_tile(g.ctx) == (width, 5)
+        ev.lbm_set_tile(g.ctx, width, 7)
+        assert ev.lbm_get_tile(g.ctx) == (width, 7)
+        with pytest.raises(ev.LBMError):
+            ev.lbm_set_tile(g.ctx, 48 - width, 7)
+        g.step(2)
+        f0, g0 = g.populations()
+        w, h = ev.lbm_autotune(g.ctx, 1)
+        assert w == width and 1 <= h <= 12 and ev.lbm_get_tile(g.ctx) == (w, h)
+        f1, g1 = g.populations()
+        assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
