@@ -38,13 +38,12 @@ namespace evlbm {
 
 namespace {
 
-constexpr int NT = 256;                           // threads per CTA, one output column each
-
-// Geometry of a TX x TY tile (TX TY = NT): region widths (x, the row stride) and sizes of
-// the tile + 3 / + 2 / + 1 halo regions of stages A / B / C, and the shared-memory layout.
+// Geometry of a TX x TY tile, one thread per output column (NT = TX TY threads; 256 run
+// two CTAs per SM, 512 one): region widths (x, the row stride) and sizes of the tile + 3 /
+// + 2 / + 1 halo regions of stages A / B / C, and the shared-memory layout.
 template <int TX_, int TY_> struct Geo {
-    static constexpr int TX = TX_, TY = TY_;
-    static_assert(TX * TY == NT, "one thread per output column");
+    static constexpr int TX = TX_, TY = TY_, NT = TX * TY, MINB = 512 / NT;
+    static_assert(NT == 256 || NT == 512, "256 or 512 threads per CTA");
     static constexpr int WA = TX + 6, WB = TX + 4, WC = TX + 2;
     static constexpr int SA = WA * (TY + 6), SB = WB * (TY + 4), SC = WC * (TY + 2);
     // Column passes of stages A and B (NT columns per pass); stage C's ring fits in one.
@@ -94,13 +93,13 @@ __device__ __forceinline__ float rcpa(float a)
 // 0..127 and 128..255 of the CTA's 256 columns (two CTAs per SM fill the 512).  In a slot,
 // population i = 9 kz + j sits at column 8 kz + j for j < 8 and at 24 + kz for j = 8, so
 // that every access starts at a multiple of its width.
-constexpr int TM_COLS = 256, TM_SLOT = 32, TM_SLOTS = 4;
-static_assert(TM_SLOTS * TM_SLOT <= TM_COLS / 2, "stash slots exceed a warp's column half");
+constexpr int TM_WARP_COLS = 128, TM_SLOT = 32, TM_SLOTS = 4;
+static_assert(TM_SLOTS * TM_SLOT <= TM_WARP_COLS, "stash slots exceed a warp's columns");
 
 __device__ __forceinline__ uint32_t tm_addr(uint32_t base, int t)
 {
     const int w = t >> 5;
-    return tmem::lane_base(base, w) + (uint32_t)((w >> 2) * (TM_COLS / 2));
+    return tmem::lane_base(base, w) + (uint32_t)((w >> 2) * TM_WARP_COLS);
 }
 // Warp-collective (.sync.aligned): every thread of the warp executes these (they
 // reconverge the warp first).
@@ -221,11 +220,12 @@ __device__ __forceinline__ void psi3_poly(float A0, float A1, float A2, float ou
 // storage spills ~190 B per thread at that budget; one CTA per SM with 245 registers and
 // no spill was measured slower (2.11 against 2.49 GLUPS at 256^3).
 template <bool THERMAL, typename S>
-__global__ void __launch_bounds__(NT, 2) k_fused3d(const Args<S> A)
+__global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3d(const Args<S> A)
 {
     constexpr bool DEV = Store<S>::dev;
     using G = typename TileOf<S>::G;
-    constexpr int TX = G::TX, TY = G::TY, WA = G::WA, WB = G::WB, WC = G::WC;
+    constexpr int TX = G::TX, TY = G::TY, NT = G::NT, WA = G::WA, WB = G::WB, WC = G::WC;
+    constexpr uint32_t TM_COLS = NT;                      // 128 columns per warp of a lane quarter
     constexpr int SA = G::SA, SB = G::SB, SC = G::SC, PA = G::PA, PB = G::PB;
     extern __shared__ float sm[];
     const int t = threadIdx.x;
@@ -695,7 +695,7 @@ cudaError_t launch(const Args<S> &A, cudaStream_t st)
         attr_dev = dev;
     }
     const dim3 grid((A.nx + G::TX - 1) / G::TX, (A.ny + G::TY - 1) / G::TY, (A.nz + A.HZ - 1) / A.HZ);
-    k_fused3d<THERMAL, S><<<grid, NT, G::SMEM_BYTES, st>>>(A);
+    k_fused3d<THERMAL, S><<<grid, G::NT, G::SMEM_BYTES, st>>>(A);
     return cudaGetLastError();
 }
 
