@@ -9,8 +9,8 @@
 //
 // Work decomposition (2.5-D z-marching).  A CTA owns a tile of 256 (x, y) output columns
 // (32 x 8 with FP32 storage, 16 x 16 with 16-bit storage, see TileOf) of one z-chunk and
-// walks its planes one per iteration; four
-// stages lag by one plane because the collision needs u and T within radius 1,
+// walks its planes one per iteration; four stages lag by one plane because the
+// collision needs u and T within radius 1,
 // hence F within radius 1, hence the Korteweg stress within radius 2, hence rho
 // within radius 3:
 //   A: rho, j (plane q)            pulled f           on the tile + 3 halo columns
@@ -89,8 +89,9 @@ __device__ __forceinline__ float rcpa(float a)
 // Tensor memory as a per-thread stash (no tensor-core work here).  Stage A pulls the 27 f
 // of the thread's own tile column three planes before stage D collides that node; the
 // values wait in TMEM instead of being pulled from L2/DRAM a second time.  4 plane slots
-// of 32 columns per thread; the two warps of a lane quarter (w and w + 4) use column halves
-// 0..127 and 128..255 of the CTA's 256 columns (two CTAs per SM fill the 512).  In a slot,
+// of 32 columns per thread; the warps of a lane quarter (w, w + 4, ...) use consecutive
+// 128-column blocks of the CTA's NT columns (256 threads: two CTAs per SM fill the 512;
+// 512 threads: one).  In a slot,
 // population i = 9 kz + j sits at column 8 kz + j for j < 8 and at 24 + kz for j = 8, so
 // that every access starts at a multiple of its width.
 constexpr int TM_WARP_COLS = 128, TM_SLOT = 32, TM_SLOTS = 4;
