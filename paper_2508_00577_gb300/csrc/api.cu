@@ -272,7 +272,7 @@ int lbm_step(lbm_ctx *c, int n_steps)
         cudaError_t e;
         if (fused)
             e = evlbm::fused2d_step(c->P.precision, c->K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx], c->RT_iso,
-                                    c->stream);
+                                    c->R[c->cur], c->R[nx], c->stream);
         else if (fused3)
             e = evlbm::fused3d_step(c->P.precision, c->K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx], c->RT_iso,
                                     c->R[c->cur], c->R[nx], c->stream);
@@ -374,7 +374,7 @@ long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
 
 long long lbm_bounds_violations(void)
 {
-    const long long v[3] = {evlbm::fused2d_oob(), evlbm::fused3d_oob(), evlbm::batch_oob()};
+    const long long v[4] = {evlbm::fused2d_oob(), evlbm::fused2d16_oob(), evlbm::fused3d_oob(), evlbm::batch_oob()};
     long long total = 0;
     for (long long x : v) {
         if (x < 0) return x;
@@ -529,7 +529,7 @@ int lbm_autotune(lbm_ctx *c, int probe_steps, int *tile_w, int *tile_h)
                 if (s == 1) e = cudaEventRecord(e0, c->stream);
                 if (e == cudaSuccess)
                     e = evlbm::fused2d_step(c->P.precision, K, c->f[c->cur], c->g[c->cur], c->f[nx], c->g[nx],
-                                            c->RT_iso, c->stream);
+                                            c->RT_iso, c->R[c->cur], c->R[nx], c->stream);
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);

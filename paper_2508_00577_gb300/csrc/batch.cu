@@ -119,6 +119,8 @@ __global__ void __launch_bounds__(threads_of<kW>(), Shape<kW>::MINB) k_batch(Bat
         A.fo = (odd ? const_cast<float *>(B.popA_f) : B.popB_f) + D.off;
         A.go = THERMAL ? (odd ? const_cast<float *>(B.popA_g) : B.popB_g) + D.off : nullptr;
         A.RT_iso = THERMAL ? nullptr : B.RT_iso + D.foff;
+        A.Rin = nullptr;
+        A.Rout = nullptr;
         A.nx = D.nx;
         A.ny = D.ny;
         A.nz = 1;

@@ -57,8 +57,13 @@ int fused3d_tile_w(int prec);
 bool fused3d_supported(int prec, int Q, const KParams &p);
 cudaError_t fused3d_step(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
                          const void *RT_iso, const void *Rin, void *Rout, cudaStream_t st);
+// Fused single-pass D2Q9 step (FP32 arithmetic, divergence force form; storage prec 1/2/3,
+// 16-bit storage reading Rin and writing Rout; wall columns with FP32 storage only).
 cudaError_t fused2d_step(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
-                         const void *RT_iso, cudaStream_t st);
+                         const void *RT_iso, const void *Rin, void *Rout, cudaStream_t st);
+// Its 16-bit storage instantiations (fused2d16.cu).
+cudaError_t fused2d_step16(int prec, const KParams &p, const void *f, const void *g, void *fo, void *go,
+                           const void *RT_iso, const void *Rin, void *Rout, cudaStream_t st);
 
 // FP64 totals of the state (mass, momentum x/y/z, energy) and a non-finite flag.
 // `work` must hold at least totals_work_bytes(N) bytes.
@@ -78,6 +83,7 @@ void interface(int eos, double a, double b, double RT, double kappa, double rv, 
 // (-DEVLBM_BOUNDS_CHECK): the count, -1 when the library was built without the
 // checks, -2 on a CUDA error.
 long long fused2d_oob();
+long long fused2d16_oob();
 long long fused3d_oob();
 long long batch_oob();
 

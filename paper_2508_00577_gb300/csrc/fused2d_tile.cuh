@@ -34,6 +34,7 @@
 #pragma once
 
 #include "bounds.cuh"
+#include "dev16.cuh"
 #include "dispatch.h"
 
 namespace evlbm {
@@ -82,8 +83,10 @@ template <int W> constexpr size_t smem_of()
 }
 
 struct FusedArgs {
-    const float *f, *g;
+    const float *f, *g;          // FP32 populations, or the raw 16-bit deviations (16-bit storage)
     float *fo, *go;
+    const float *Rin;            // 16-bit storage: reference records read (dev16.cuh) ...
+    float *Rout;                 // ... and written
     const float *RT_iso;
     int nx, ny, nz, H;
     unsigned N;                  // nodes of the lattice (Q*N < 2^31)
@@ -136,6 +139,32 @@ __device__ __forceinline__ void pull_own(const float *__restrict__ base, unsigne
     }
 }
 
+// Store of one encoded 16-bit deviation (streaming: not read again this step).
+template <typename S> __device__ __forceinline__ void st16(float *base, unsigned idx, float v)
+{
+    __stcs(reinterpret_cast<unsigned short *>(base) + idx, Bits16<S>::from_f(v));
+}
+
+// 16-bit storage: the pulled populations of rows (r, r+1) of one column, each rebuilt from
+// its source node's reference record and its stored deviation (G: energy populations).
+template <typename S, bool G>
+__device__ __forceinline__ void pull18_dev(const float *base_, const float *R, unsigned N, const unsigned ro[4],
+                                           const int cols[3], v2 h[9])
+{
+    const unsigned short *base = reinterpret_cast<const unsigned short *>(base_);
+    auto one = [&](int cx, int cy, unsigned i, unsigned n) {
+        if (!(in_bounds(i * N + n, 9ull * N) && in_bounds(n, N))) return 0.f;
+        const float d = Bits16<S>::to_f(__ldg(base + i * N + n));
+        const Ref16 r = load_rec(R, N, n);
+        return G ? decode_g<9>(cx, cy, 0, r, d) : decode_f<9>(cx, cy, 0, r, d);
+    };
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = i % 3 - 1, cy = i / 3 - 1;
+        h[i] = V(one(cx, cy, i, ro[1 - cy] + cols[1 - cx]), one(cx, cy, i, ro[2 - cy] + cols[1 - cx]));
+    }
+}
+
 __device__ __forceinline__ v2 sum9(const v2 h[9])
 {
     return ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
@@ -146,9 +175,13 @@ __device__ __forceinline__ v2 sum9(const v2 h[9])
 // written by other CTAs of the same launch.  A CTA that runs several tiles must pass a
 // barrier between them (the rings are reused).  WALLS compiles in the wall columns
 // (FusedArgs::walls); without it the kernel has no trace of them.
-template <int kW, bool THERMAL, bool CG, bool WALLS = false>
+template <int kW, bool THERMAL, bool CG, bool WALLS = false, typename ST = float>
 __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, int rows, int bz, v2 *smem)
 {
+    // 16-bit deviation storage (ST = __half / __nv_bfloat16): pulls decode, stage D encodes
+    // against the node's new reference record (dev16.cuh); no wall columns, no ensemble.
+    constexpr bool DEV = Store<ST>::dev;
+    static_assert(!(DEV && (WALLS || CG)), "16-bit storage runs the single-lattice kernel without walls");
     constexpr int S = slots_of<kW>();
     enum { RHO, JX, JY, PXX, PXY, PYY, UX, UY, QX, QY, WQ };
     auto fld = [&](int field, int slot3) -> v2 * { return smem + (field * kDepth + slot3) * S; };
@@ -200,9 +233,16 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
 
     const float a = A.a, b = A.b, kappa = A.kappa, lambda = A.lambda;
     const unsigned N = A.N;
-    auto pull = [&](const float *base, const unsigned ro[4], v2 h[9]) {
-        if (wallc) pull_own<CG>(base, N, ro, cols[1], h);
-        else pull18<CG>(base, N, ro, cols, h);
+    // gp: energy populations (the decoding of 16-bit storage differs).
+    auto pull = [&](const float *base, const unsigned ro[4], v2 h[9], bool gp) {
+        if constexpr (DEV) {
+            if (gp) pull18_dev<ST, true>(base, A.Rin, N, ro, cols, h);
+            else pull18_dev<ST, false>(base, A.Rin, N, ro, cols, h);
+        } else if (wallc) {
+            pull_own<CG>(base, N, ro, cols[1], h);
+        } else {
+            pull18<CG>(base, N, ro, cols, h);
+        }
     };
     auto rows4 = [&](int r, unsigned ro[4]) {      // rows r-1 .. r+2 of the layer
         const int rp = next_row(r, ny);
@@ -225,12 +265,12 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
     if (inA) {
         unsigned ro[4];
         rows4(rA, ro);
-        pull(A.f, ro, pf);
+        pull(A.f, ro, pf, false);
     }
     if (THERMAL && inC) {
         unsigned ro[4];
         rows4(rC, ro);
-        pull(A.g, ro, pg);
+        pull(A.g, ro, pg, true);
     }
 
     for (int q = qbeg; q <= qend; ++q) {
@@ -268,7 +308,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
             if (q < qend) {
                 unsigned ro[4];
                 rows4(rA, ro);
-                pull(A.f, ro, pf);
+                pull(A.f, ro, pf, false);
             }
         }
         __syncthreads();
@@ -335,7 +375,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
                 if (q + 1 <= qend) {           // prefetch the next stage-C pair
                     unsigned ro[4];
                     rows4(rC, ro);
-                    pull(A.g, ro, pg);
+                    pull(A.g, ro, pg, true);
                 }
             } else {
                 const float *Tp = A.RT_iso + layer + cols[1];
@@ -482,13 +522,30 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
             const unsigned out0 = layer + (unsigned)rD * nx + cols[1];
             const unsigned out1 = layer + (unsigned)next_row(rD, ny) * nx + cols[1];
             const bool second = 2 * p + 1 < y0 + Heff;
+            // 16-bit storage: the node's new reference records (rho, u, theta0, e) for both rows
+            // and the equilibria the deviations are taken against (dev16.cuh).
+            EncTab tab0, tab1;
+            if constexpr (DEV) {
+                const Ref16 r0 = make_rec(rho.x, ux.x, uy.x, 0.f, th.x, RT.x);
+                const Ref16 r1 = make_rec(rho.y, ux.y, uy.y, 0.f, th.y, RT.y);
+                enc_tab<9>(r0, THERMAL, tab0);
+                enc_tab<9>(r1, THERMAL, tab1);
+                if (in_bounds(out0, N)) store_rec(A.Rout, N, out0, r0);
+                if (second && in_bounds(out1, N)) store_rec(A.Rout, N, out1, r1);
+            }
             const v2 *fr = f9 + (p & 3) * 9 * kW + t;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const int ix = i % 3, iy = i / 3;
                 const v2 o = fma2(kh, fr[i * kW], fma2(exk[ix], ey[iy], sxk[ix] * sy[iy]));
-                if (in_bounds(i * N + out0, 9ull * N)) A.fo[i * N + out0] = o.x;
-                if (second && in_bounds(i * N + out1, 9ull * N)) A.fo[i * N + out1] = o.y;
+                if constexpr (DEV) {
+                    if (in_bounds(i * N + out0, 9ull * N)) st16<ST>(A.fo, i * N + out0, encode_f<9>(ix - 1, iy - 1, 0, tab0, o.x));
+                    if (second && in_bounds(i * N + out1, 9ull * N))
+                        st16<ST>(A.fo, i * N + out1, encode_f<9>(ix - 1, iy - 1, 0, tab1, o.y));
+                } else {
+                    if (in_bounds(i * N + out0, 9ull * N)) A.fo[i * N + out0] = o.x;
+                    if (second && in_bounds(i * N + out1, 9ull * N)) A.fo[i * N + out1] = o.y;
+                }
             }
             if constexpr (THERMAL) {
                 // g^eq_i = rho [e PsiP_x PsiP_y + PsiS_x PsiP_y + PsiP_x PsiS_y], e = 3/2 RT,
@@ -530,8 +587,15 @@ __device__ __forceinline__ void fused_tile(const FusedArgs &A, int bx, int y0, i
                     if (i == 7) c = c + hqy;   // c = (0,1)
                     c = fma2(exk[ix], Sy[iy], fma2(Ax[ix], ey[iy], c));      // + keq g^eq
                     const v2 o = fma2(kh, gr[i * kW], c);
-                    if (in_bounds(i * N + out0, 9ull * N)) A.go[i * N + out0] = o.x;
-                    if (second && in_bounds(i * N + out1, 9ull * N)) A.go[i * N + out1] = o.y;
+                    if constexpr (DEV) {
+                        if (in_bounds(i * N + out0, 9ull * N))
+                            st16<ST>(A.go, i * N + out0, encode_g<9>(ix - 1, iy - 1, 0, tab0, o.x));
+                        if (second && in_bounds(i * N + out1, 9ull * N))
+                            st16<ST>(A.go, i * N + out1, encode_g<9>(ix - 1, iy - 1, 0, tab1, o.y));
+                    } else {
+                        if (in_bounds(i * N + out0, 9ull * N)) A.go[i * N + out0] = o.x;
+                        if (second && in_bounds(i * N + out1, 9ull * N)) A.go[i * N + out1] = o.y;
+                    }
                 }
             }
             rD = next_row(next_row(rD, ny), ny);

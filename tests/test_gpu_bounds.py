@@ -2,7 +2,8 @@
 every global and shared-memory index they use with the extent of its array, count an
 index out of range and skip the access.  Ragged lattices through every launch shape of
 the D2Q9 kernel, z-chunks of the D3Q27 kernel that do not divide nz (FP32 and 16-bit
-storage), the D2Q9 kernel's wall columns on a ragged strip, and an ensemble of small
+storage), 16-bit storage through the D2Q9 kernel, the D2Q9 kernel's wall columns on a
+ragged strip, and an ensemble of small
 uneven domains must meet no such index, and the checked library must still agree with
 the FP64 oracle (1e-5; 1e-3 for 16-bit storage).  The checked library runs in a child process (EVLBM_LIBRARY)."""
 import json
@@ -65,6 +66,19 @@ for (nx, ny, nz, hz) in [(20, 18, 11, 4), (33, 16, 7, 3), (5, 3, 4, 1), (17, 17,
                 ev.lbm_set_tile(g.ctx, 0, hz)
                 g.step(4)
                 check(f"d3q27 {tag} {nx}x{ny}x{nz} z-chunk {hz}", o, g.moments()[0])
+# 16-bit storage through the fused D2Q9 kernel: ragged strips, a chunk height that does not
+# divide ny, the balanced grid.
+for (nx, ny, nz) in [(130, 70, 2), (7, 5, 1)]:
+    for W, H in ((128, 6), (64, ev.LBM_TILE_BALANCED)):
+        f = inputs.spinodal_noise(nx, ny, nz, 0.5 * (s1 + s2), RT, amplitude=0.05, D=2)
+        o = oracle.State(oracle.Params(Q=9, nx=nx, ny=ny, nz=nz, eos=E.CS, a=A, b=B, kappa=kappa, tau=0.3), *f)
+        o.step(5)
+        for prec, tag in ((ev.LBM_FP16_DEV, "fp16"), (ev.LBM_BF16_DEV, "bf16")):
+            p16 = ev.lbm_params.make(nx=nx, ny=ny, nz=nz, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=kappa, precision=prec)
+            with ev.Lattice(p16, *f) as g:
+                ev.lbm_set_tile(g.ctx, W, H)
+                g.step(5)
+                check(f"d2q9 {tag} {nx}x{ny}x{nz} W{W} H{H}", o, g.moments()[0])
 # Wall columns of the fused D2Q9 kernel (thermal Couette set-up, kappa = 0), ragged strip.
 for H in (4, ev.LBM_TILE_BALANCED):
     nx, ny = 33, 5
@@ -115,7 +129,7 @@ def test_checked_library_meets_no_out_of_range_index():
     assert r.returncode == 0, r.stderr[-3000:]
     res = json.loads(r.stdout.split("RESULT ", 1)[1])
     assert res["start"] == 0
-    assert len(res["cases"]) == 4 * 4 * 4 + 4 + 2 * 2 + 2 + 3
+    assert len(res["cases"]) == 4 * 4 * 4 + 4 + 2 * 2 + 2 * 2 * 2 + 2 + 3
     for name, err, oob in res["cases"]:
         assert oob == 0, f"{name}: {oob} out-of-range indices"
         assert err <= (1e-3 if ("fp16" in name or "bf16" in name) else 1e-5), f"{name}: max rel rho error {err}"

@@ -270,6 +270,32 @@ def test_reduced_precision_d2q9(precision, nx, ny, nz):
     assert_fields(o, g, TOL[precision])
 
 
+@pytest.mark.parametrize("precision", [ev.LBM_FP16_DEV, ev.LBM_BF16_DEV])
+@pytest.mark.parametrize("nx,ny,nz,thermal", [(130, 70, 2, 1), (7, 5, 1, 1), (200, 33, 1, 0)])
+def test_reduced_precision_d2q9_fused_launch_shapes(precision, nx, ny, nz, thermal):
+    """16-bit storage through the fused D2Q9 kernel (one launch per step) on every strip
+    width, a chunk height that does not divide ny and the balanced persistent grid:
+    rho and T within 1e-3 relative, u within 1e-4 of the FP64 oracle after 20 steps."""
+    fields, kappa = droplet_fields(nx, ny, nz, tr=0.9 if not thermal else 0.8)
+    o = oracle.State(oracle.Params(Q=9, nx=nx, ny=ny, nz=nz, eos=E.CS, a=A, b=B, kappa=kappa, tau=0.3,
+                                   thermal=thermal), *fields)
+    o.step(20)
+    ro, uo, To, _ = o.macro()
+    for W in (64, 128, 192):
+        for H in (6, ev.LBM_TILE_BALANCED):
+            gp = ev.lbm_params.make(nx=nx, ny=ny, nz=nz, eos=E.CS, a=A, b=B, kappa=kappa, tau=0.3,
+                                    thermal=thermal, precision=precision)
+            with ev.Lattice(gp, *fields) as g:
+                assert ev.lbm_launches_per_step(g.ctx) == 1
+                ev.lbm_set_tile(g.ctx, W, H)
+                g.step(20)
+                rg, ug, Tg, _ = g.moments()
+            er = float(np.max(np.abs(rg - ro) / ro))
+            eT = float(np.max(np.abs(Tg - To) / To))
+            eu = float(np.max(np.abs(ug.reshape(uo.shape) - uo)))
+            assert er <= 1e-3 and eT <= 1e-3 and eu <= 1e-4, (W, H, er, eT, eu)
+
+
 def test_fp32_long_run_droplet():
     """FP32 storage rounds every population once per step, so the FP32 - FP64 density
     difference drifts by about one FP32 ulp per step; over 2000 steps (128^2, R = 32)
