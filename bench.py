@@ -393,7 +393,11 @@ def run_sweep16(args):
                                tau=TAU, lambda_=1.0, thermal=1, precision=prec)
         stream = torch.cuda.Stream()
         with ev.Lattice(p, rho, u, T, stream=stream.cuda_stream) as g:
-            tile = ev.lbm_autotune(g.ctx, 3)
+            if args.tile:                       # fixed W,H launch shape (the one a profile captures)
+                ev.lbm_set_tile(g.ctx, *(int(v) for v in args.tile.split(",")))
+                tile = ev.lbm_get_tile(g.ctx)
+            else:
+                tile = ev.lbm_autotune(g.ctx, 3)
             g.step(args.warmup)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -924,8 +928,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and 3-D measurements in the default run")
     ap.add_argument("--tile", default="", help="fixed launch shape W,H of the fused kernel")
     ap.add_argument("--log", default="", help="also append each result line to this JSON-lines file")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "surrogate", "surrogate_kernels", "spinodal3d",
-                                                         "laplace", "couette",
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "sweep16", "ensemble", "surrogate", "surrogate_kernels",
+                                                         "spinodal3d", "laplace", "couette",
                                                            "coexistence"],
                     help="sweep: the headline droplet Laplace sweep; ensemble: 512 uneven domains; "
                          "surrogate: U-Net surrogate with lattice Boltzmann fallback vs plain LB")
@@ -956,6 +960,13 @@ def main():
         return run_surrogate_kernels(args)
     if args.workload == "spinodal3d":
         emit(run_spinodal3d(args), args)
+        return 0
+    if args.workload == "sweep16":
+        line = run_sweep16(args)
+        line.update({"metric": "MLUPS", "value": line["fp16"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
+                     "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f16",
+                     "data": "synthetic"})
+        emit(line, args)
         return 0
     if args.workload == "coexistence":
         emit(run_coexistence(args), args)
