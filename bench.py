@@ -301,7 +301,9 @@ def run(args):
                 "population changes by sum(u.F) per step (Eq. T_shift), mass and momentum are conserved"}
 
     # End to end through the public API with host buffers: init (H2D) + steps + moments (D2H).
-    e2e_steps = args.steps
+    # The end-to-end job runs at least 2000 steps (a tenth of the sweep's 20000), so that a
+    # short timed window (--steps) does not turn it into a measurement of lbm_init alone.
+    e2e_steps = max(args.steps, 2000)
     pinned = [torch.from_numpy(a).pin_memory().numpy() for a in (rho, u.reshape(-1), T)]
     out_rho = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
     torch.cuda.synchronize(dev)

@@ -99,9 +99,12 @@ typedef struct {
  * The populations start at f = f^eq(rho, u, P0/rho) and g = g^eq(rho, u, RT)
  * (Eqs. feq, geq), so the raw momentum is rho u and the first step sees the
  * shifted velocity u + F/(2 rho) (Eq. u_shift).
- * `stream` is a cudaStream_t (or NULL).  On success *out receives the context.
+ * `stream` is a cudaStream_t (or NULL).  The fields are copied to the device as they
+ * are (DMA when the host arrays are pinned) and checked and converted there; the call
+ * returns after the initial state is built.  On success *out receives the context.
  * Errors: LBM_EINVAL (bad parameters or pointers), LBM_ENOMEM, LBM_ECUDA,
- * LBM_ENONFINITE (non-finite or non-positive rho, non-positive T). */
+ * LBM_ENONFINITE (non-finite or non-positive rho, non-finite or non-positive T,
+ * non-finite u; the message names the lowest such node). */
 int lbm_init(const lbm_params *params, const double *rho, const double *u, const double *T,
              void *stream, lbm_ctx **out);
 

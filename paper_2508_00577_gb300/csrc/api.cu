@@ -159,6 +159,25 @@ __global__ void k_scale_field(const float *T, float R, long long N, float *RT)
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x)
         RT[n] = R * T[n];
 }
+// Initial fields, FP64 as the caller passed them (rho [N], u [D][N], T [N]), checked and
+// converted on the device: out = (rho, u, R T) in the scratch precision; *bad = the lowest
+// node with rho or T not finite and > 0 or u not finite (left at N when all are valid).
+template <typename real>
+__global__ void k_prepare_fields(const double *in, int D, long long N, double R, real *out, long long *bad)
+{
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const double rho = in[n], T = in[(D + 1) * N + n];
+        bool ok = rho > 0.0 && isfinite(rho) && T > 0.0 && isfinite(T);
+        for (int a = 0; a < D; ++a) {
+            const double v = in[(1 + a) * N + n];
+            ok = ok && isfinite(v);
+            out[(1 + a) * N + n] = real(v);
+        }
+        out[n] = real(rho);
+        out[(D + 1) * N + n] = real(R * T);
+        if (!ok) atomicMin(reinterpret_cast<unsigned long long *>(bad), (unsigned long long)n);
+    }
+}
 }  // namespace
 
 extern "C" {
@@ -185,18 +204,6 @@ int lbm_init(const lbm_params *params, const double *rho, const double *u, const
     const long long N = c->N;
     const int D = c->D;
 
-    // Host-side checks of the initial fields.
-    for (long long n = 0; n < N; ++n) {
-        if (!(rho[n] > 0.0) || !isfinite(rho[n]) || !(T[n] > 0.0) || !isfinite(T[n])) {
-            free(c);
-            return fail(nullptr, LBM_ENONFINITE, "rho and T must be finite and > 0 (node %lld)", n);
-        }
-        for (int a = 0; a < D; ++a)
-            if (!isfinite(u[a * N + n])) {
-                free(c);
-                return fail(nullptr, LBM_ENONFINITE, "u must be finite (node %lld)", n);
-            }
-    }
     fill_kparams(c);
 
     // Device state.
@@ -209,32 +216,48 @@ int lbm_init(const lbm_params *params, const double *rho, const double *u, const
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->red, evlbm::totals_work_bytes(N));
     if (e == cudaSuccess) e = cudaMalloc(&c->RT_iso, c->real_bytes * (size_t)N);
-    void *d_fields = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&d_fields, c->real_bytes * (size_t)(D + 2) * (size_t)N);
+    // The caller's FP64 fields go to the device as they are (one copy each, DMA when the
+    // host arrays are pinned), followed by the index word; the check and the conversion to
+    // the scratch precision -- rho [N], u [D][N], RT [N] = R T -- run in one kernel.
+    const size_t nf = (size_t)(D + 2) * (size_t)N;
+    void *d_fields = nullptr, *d_in = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d_fields, c->real_bytes * nf);
+    if (e == cudaSuccess) e = cudaMalloc(&d_in, sizeof(double) * nf + sizeof(long long));
     if (e != cudaSuccess) {
         const int code = cuda_fail(nullptr, e, "lbm_init allocation");
         if (d_fields) cudaFree(d_fields);
+        if (d_in) cudaFree(d_in);
         free_all(c);
         free(c);
         return code;
     }
-
-    // Fields in the scratch precision: rho [N], u [D][N], RT [N] = R*T.
-    const size_t nf = (size_t)(D + 2) * (size_t)N;
-    if (c->real_bytes == 8) {
-        std::vector<double> h(nf);
-        memcpy(h.data(), rho, sizeof(double) * N);
-        memcpy(h.data() + N, u, sizeof(double) * D * N);
-        for (long long n = 0; n < N; ++n) h[(D + 1) * N + n] = params->R * T[n];
-        e = cudaMemcpyAsync(d_fields, h.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    } else {
-        std::vector<float> h(nf);
-        for (long long n = 0; n < N; ++n) h[n] = float(rho[n]);
-        for (long long k = 0; k < D * N; ++k) h[N + k] = float(u[k]);
-        for (long long n = 0; n < N; ++n) h[(D + 1) * N + n] = float(params->R * T[n]);
-        e = cudaMemcpyAsync(d_fields, h.data(), sizeof(float) * nf, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    double *din = static_cast<double *>(d_in);
+    long long *d_bad = reinterpret_cast<long long *>(din + nf);
+    long long bad = N;
+    e = cudaMemcpyAsync(din, rho, sizeof(double) * N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(din + N, u, sizeof(double) * D * N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(din + (D + 1) * N, T, sizeof(double) * N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_bad, &bad, sizeof(bad), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        long long blocks = (N + 255) / 256;
+        if (blocks > 8192) blocks = 8192;
+        if (c->real_bytes == 8)
+            k_prepare_fields<double><<<(int)blocks, 256, 0, c->stream>>>(din, D, N, params->R,
+                                                                         static_cast<double *>(d_fields), d_bad);
+        else
+            k_prepare_fields<float><<<(int)blocks, 256, 0, c->stream>>>(din, D, N, params->R,
+                                                                        static_cast<float *>(d_fields), d_bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_in);
+    if (e == cudaSuccess && bad < N) {
+        cudaFree(d_fields);
+        free_all(c);
+        free(c);
+        return fail(nullptr, LBM_ENONFINITE, "rho and T must be finite and > 0 and u finite (node %lld)", bad);
     }
     const char *dF = static_cast<const char *>(d_fields);
     const void *d_rho = dF, *d_u = dF + c->real_bytes * N, *d_RT = dF + c->real_bytes * (D + 1) * N;

@@ -425,3 +425,29 @@ def test_d3q27_tile_shape_per_storage(prec, width):
         assert w == width and 1 <= h <= 12 and ev.lbm_get_tile(g.ctx) == (w, h)
         f1, g1 = g.populations()
         assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+
+
+@pytest.mark.parametrize("precision", [ev.LBM_FP64, ev.LBM_FP32, ev.LBM_BF16_DEV])
+def test_init_checks_fields_on_the_device(precision):
+    """lbm_init checks the initial fields on the device: a non-positive or non-finite
+    density or temperature, or a non-finite velocity, is LBM_ENONFINITE naming the lowest
+    such node; a valid set afterwards initialises normally and gives the oracle's state."""
+    fields, kappa = droplet_fields(40, 30, 1)
+    gp = ev.lbm_params.make(nx=40, ny=30, kappa=kappa, precision=precision)
+    rho, u, T = (np.array(a, dtype=np.float64) for a in fields)
+    cases = []
+    r = rho.copy(); r[37] = 0.0; T2 = T.copy(); T2[500] = np.nan
+    cases.append(((r, u, T2), 37))
+    u2 = u.copy(); u2[1, 11] = np.inf
+    cases.append(((rho, u2, T), 11))
+    T3 = T.copy(); T3[1199] = -1.0
+    cases.append(((rho, u, T3), 1199))
+    for bad_fields, node in cases:
+        with pytest.raises(ev.LBMError) as e:
+            ev.Lattice(gp, *bad_fields)
+        assert e.value.code == ev.LBM_ENONFINITE and f"node {node}" in str(e.value), str(e.value)
+    o, g = pair(9, 40, 30, 1, fields, kappa, precision)
+    with g:
+        ro = o.macro()[0]
+        rg = g.moments()[0]
+    assert float(np.max(np.abs(rg - ro) / ro)) <= (1e-15 if precision == ev.LBM_FP64 else 1e-3)
