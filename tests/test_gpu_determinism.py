@@ -28,6 +28,7 @@ def spinodal(nx, ny, nz, D):
     (ev.LBM_D2Q9, 300, 130, 2, ev.LBM_FP32),
     (ev.LBM_D3Q27, 40, 35, 19, ev.LBM_FP32),
     (ev.LBM_D2Q9, 96, 80, 1, ev.LBM_FP16_DEV),
+    (ev.LBM_D3Q27, 33, 20, 13, ev.LBM_BF16_DEV),
 ])
 def test_two_runs_are_bit_identical(lattice, nx, ny, nz, precision):
     fields, kappa = spinodal(nx, ny, nz, 2 if lattice == ev.LBM_D2Q9 else 3)
