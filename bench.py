@@ -633,10 +633,11 @@ def run_surrogate(args):
 
     # Rollouts: the surrogate alone, and with the fallback at a sweep of liquid-count
     # thresholds (mass projected, so the mass indicator is a safeguard only).
-    configs = [("surrogate_only", 1e30, 1e30, False)]
-    configs += [(f"fallback_area_{a:g}", args.max_mass_drift, a, True) for a in args.area_sweep]
+    configs = [("surrogate_only", 1e30, 1e30, False, 1.0)]
+    configs += [(f"fallback_area_{a:g}", args.max_mass_drift, a, True, 1.0) for a in args.area_sweep]
+    configs += [(f"fallback_interface_{f:g}", args.max_mass_drift, 1e30, True, f) for f in args.shift_sweep]
     results = {}
-    for name, dm, da, proj in configs:
+    for name, dm, da, proj, shift in configs:
         with ev.Lattice(params(nd), rho0, u0, T0) as lb:
             ev.lbm_set_tile(lb.ctx, *tile)
             d = start.clone()
@@ -644,7 +645,7 @@ def run_surrogate(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             try:
-                nfb, used = model.rollout(lb.ctx, d.data_ptr(), nd, SUR_WINDOWS, SUR_STEPS, rho_mid, dm, da, proj)
+                nfb, used = model.rollout(lb.ctx, d.data_ptr(), nd, SUR_WINDOWS, SUR_STEPS, rho_mid, dm, da, proj, shift)
                 failed = None
             except S.SurError as exc:
                 nfb, failed = -1, str(exc)
@@ -675,7 +676,8 @@ def run_surrogate(args):
         "config": {"workload": f"{nd} held-out droplet-pair domains of {SUR_N}^2, {steps} steps = {SUR_WINDOWS} windows "
                                f"of {SUR_STEPS}; trained on {len(train_doms)} domains x {SUR_WINDOWS} windows",
                    "kappa": SUR_KAPPA, "tau": TAU, "train_steps": args.train_steps, "batch": bs,
-                   "max_mass_drift": args.max_mass_drift, "area_sweep": args.area_sweep},
+                   "max_mass_drift": args.max_mass_drift, "area_sweep": args.area_sweep,
+                   "interface_shift_sweep": args.shift_sweep},
         "plain_lb_seconds": t_lb, "plain_lb_mlups": N * steps / t_lb / 1e6,
         "rollouts": results,
         "inference": {"ms_per_window": t_inf * 1e3, "tflops": flops / t_inf / 1e12, "batch": nd},
@@ -945,6 +947,8 @@ def main():
     ap.add_argument("--lr", type=float, default=3e-4)
     ap.add_argument("--max-mass-drift", type=float, default=1e-3)
     ap.add_argument("--area-sweep", type=float, nargs="+", default=[0.02, 0.005, 0.001])
+    ap.add_argument("--shift-sweep", type=float, nargs="+", default=[0.01, 0.002],
+                    help="surrogate: thresholds of the interface-position indicator (fraction of nodes changing phase)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = ENSEMBLE_STEPS if args.workload == "ensemble" and args.impl == "native" else 2000

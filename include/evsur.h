@@ -186,7 +186,11 @@ int sur_indicators(const float *d_fields, int batch, int H, int W, float rho_mid
  * any domain, a field is not finite or rho or T is not positive, the mass
  * differs from the start by more than max_mass_drift (relative), or the liquid
  * node count (rho > rho_mid) differs from the previous window's by more than
- * max_area_change (relative); the window is then advanced by the lattice
+ * max_area_change (relative), or more than a fraction max_interface_shift of the
+ * domain's nodes change phase (rho above / below rho_mid) against the current
+ * fields -- an interface-position indicator, which also sees interfaces that move
+ * without changing the liquid count (1 or more: off); the window is then advanced
+ * by the lattice
  * Boltzmann context lb instead (nz = batch layers of H x W, D2Q9, not FP64).
  * The first fallback window and every fallback window that follows an accepted
  * surrogate window restart lb from the local equilibrium of the current fields
@@ -201,6 +205,7 @@ typedef struct sur_rollout_cfg {
     int windows, steps;
     float rho_mid, max_mass_drift, max_area_change;
     int project_mass;
+    float max_interface_shift;
 } sur_rollout_cfg;
 int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur_rollout_cfg *cfg,
                 unsigned char *h_used_lb, int *n_fallback);

@@ -774,9 +774,11 @@ int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur
     const long long Mb = (long long)m->H * m->W, N = Mb * batch;
     int rc = ensure_batch(m, batch, m->train_buffers);
     if (rc) return rc;
-    if (!m->ind) CK(cudaMalloc(&m->ind, sizeof(double) * 2 * 4096 + sizeof(float) * 4096));
-    float *d_delta = reinterpret_cast<float *>(m->ind + 2 * 4096);
-    std::vector<double> cur(2 * batch), nxt(2 * batch), mass0(batch);
+    if (!m->ind) CK(cudaMalloc(&m->ind, sizeof(double) * 3 * 4096 + sizeof(float) * 4096));
+    double *d_flips = m->ind + 2 * 4096;
+    float *d_delta = reinterpret_cast<float *>(m->ind + 3 * 4096);
+    std::vector<double> cur(2 * batch), nxt(2 * batch), mass0(batch), flips(batch);
+    const bool use_shift = cfg->max_interface_shift < 1.f;
     std::vector<float> delta(batch);
     // Indicators of d_fields into host (v); *invalid = the invalid flag.
     auto measure = [&](const float *F, std::vector<double> &v, int *invalid) -> int {
@@ -804,9 +806,18 @@ int sur_rollout(sur_model *m, lbm_ctx *lb, float *d_fields, int batch, const sur
             CK(evsur::shift_rho(m->next, batch, Mb, d_delta, m->stream));
             if ((rc = measure(m->next, nxt, &bad))) return rc;
         }
+        // Interface position: nodes whose phase differs between the proposal and the
+        // current fields.
+        if (use_shift && !bad) {
+            CK(evsur::phase_flips(d_fields, m->next, batch, Mb, cfg->rho_mid, d_flips, m->stream));
+            CK(cudaMemcpyAsync(flips.data(), d_flips, sizeof(double) * batch, cudaMemcpyDeviceToHost, m->stream));
+            CK(cudaStreamSynchronize(m->stream));
+        }
         // Acceptance: finite and positive fields, cumulative mass drift against the
-        // start, liquid-count change against the previous window.
+        // start, liquid-count change against the previous window, interface shift.
         bool accept = !bad;
+        for (int b = 0; b < batch && accept && use_shift; ++b)
+            if (!(flips[b] <= (double)cfg->max_interface_shift * (double)Mb)) accept = false;
         for (int b = 0; b < batch && accept; ++b) {
             const double dm = fabs(nxt[2 * b] - mass0[b]) / fabs(mass0[b]);
             const double da = fabs(nxt[2 * b + 1] - cur[2 * b + 1]) / fmax(cur[2 * b + 1], 1.0);

@@ -376,6 +376,26 @@ __global__ void k_up_weights(const float *Wm, int Cin, int Cout, bf16 *Wb, bf16 
 
 // Per-domain FP64 sums of rho and of the liquid count (rho > rho_mid): out[2b],
 // out[2b+1]; invalid[0] |= 1 if any field is not finite or rho or T is not > 0.
+// Interface-position indicator: per domain, the number of nodes whose phase (rho above or
+// below rho_mid) differs between the density fields A and B (out[b] += count).
+__global__ void k_phase_flips(const float *A, const float *B, long long Mb, float rho_mid, double *out)
+{
+    __shared__ double s1[256];
+    const long long b = blockIdx.y;
+    double a = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Mb; i += (long long)gridDim.x * blockDim.x) {
+        const long long n = b * Mb + i;
+        a += ((A[n] > rho_mid) != (B[n] > rho_mid)) ? 1.0 : 0.0;
+    }
+    s1[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) s1[threadIdx.x] += s1[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out + b, s1[0]);
+}
+
 __global__ void k_indicators(const float *F, long long M, long long Mb, float rho_mid, double *out, int *invalid)
 {
     __shared__ double s1[256], s2[256];
@@ -521,6 +541,18 @@ cudaError_t indicators(const float *F, int batch, long long Mb, float rho_mid, d
     if (gx > 64) gx = 64;
     const dim3 grid((unsigned)gx, (unsigned)batch);
     k_indicators<<<grid, 256, 0, st>>>(F, (long long)batch * Mb, Mb, rho_mid, out, invalid);
+    return cudaGetLastError();
+}
+
+cudaError_t phase_flips(const float *A, const float *B, int batch, long long Mb, float rho_mid, double *out,
+                        cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * batch, st);
+    if (e != cudaSuccess) return e;
+    long long gx = (Mb + 255) / 256;
+    if (gx > 64) gx = 64;
+    const dim3 grid((unsigned)gx, (unsigned)batch);
+    k_phase_flips<<<grid, 256, 0, st>>>(A, B, Mb, rho_mid, out);
     return cudaGetLastError();
 }
 

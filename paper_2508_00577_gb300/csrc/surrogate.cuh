@@ -93,6 +93,8 @@ cudaError_t conv_weights(const float *Wt, int Cin, int Cout, int Kp, int Kpo, bf
 cudaError_t up_weights(const float *Wm, int Cin, int Cout, bf16 *Wb, bf16 *Wt, cudaStream_t st);
 cudaError_t indicators(const float *F, int batch, long long Mb, float rho_mid, double *out, int *invalid,
                        cudaStream_t st);
+cudaError_t phase_flips(const float *A, const float *B, int batch, long long Mb, float rho_mid, double *out,
+                        cudaStream_t st);
 cudaError_t shift_rho(float *rho, int batch, long long Mb, const float *delta, cudaStream_t st);
 
 }  // namespace evsur

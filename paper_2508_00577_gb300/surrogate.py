@@ -57,7 +57,7 @@ class sur_gemm_args(ctypes.Structure):
 class sur_rollout_cfg(ctypes.Structure):
     _fields_ = [("windows", ctypes.c_int), ("steps", ctypes.c_int), ("rho_mid", ctypes.c_float),
                 ("max_mass_drift", ctypes.c_float), ("max_area_change", ctypes.c_float),
-                ("project_mass", ctypes.c_int)]
+                ("project_mass", ctypes.c_int), ("max_interface_shift", ctypes.c_float)]
 
 
 _lock = threading.Lock()
@@ -184,8 +184,9 @@ def sur_indicators(d_fields, batch, H, W, rho_mid, d_out, stream=0):
 
 
 def sur_rollout(model, lb_ctx, d_fields, batch, windows, steps, rho_mid, max_mass_drift, max_area_change,
-                project_mass=False):
-    cfg = sur_rollout_cfg(windows, steps, rho_mid, max_mass_drift, max_area_change, 1 if project_mass else 0)
+                project_mass=False, max_interface_shift=1.0):
+    cfg = sur_rollout_cfg(windows, steps, rho_mid, max_mass_drift, max_area_change, 1 if project_mass else 0,
+                          max_interface_shift)
     used = (ctypes.c_ubyte * max(windows, 1))()
     nfb = ctypes.c_int(0)
     _check(lib().sur_rollout(model, lb_ctx, d_fields, batch, ctypes.byref(cfg), used, ctypes.byref(nfb)), model)
@@ -258,9 +259,9 @@ class Surrogate:
         sur_infer(self.m, d_x, d_y, batch)
 
     def rollout(self, lb_ctx, d_fields, batch, windows, steps, rho_mid, max_mass_drift=1e-3, max_area_change=0.02,
-                project_mass=False):
+                project_mass=False, max_interface_shift=1.0):
         return sur_rollout(self.m, lb_ctx, d_fields, batch, windows, steps, rho_mid, max_mass_drift, max_area_change,
-                           project_mass)
+                           project_mass, max_interface_shift)
 
     def close(self):
         if self.m:

@@ -82,14 +82,21 @@ def test_invalid_params_rejected_on_host(field, value):
     assert ev.lbm_last_error(None)
 
 
-def test_nonpositive_fields_rejected_on_host():
+def test_init_without_a_gpu_fails_cleanly():
+    """The initial fields are checked on the device (tests/test_gpu_parity.py covers the
+    check); without a usable GPU lbm_init returns LBM_ECUDA with a message, whatever the
+    fields, and leaves nothing allocated."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
     p = ev.lbm_params.make(nx=4, ny=4)
     rho = np.ones(16)
     rho[5] = -1.0
-    with pytest.raises(ev.LBMError) as e:
-        ev.lbm_init(p, rho, np.zeros((2, 16)), np.ones(16))
-    assert e.value.code == ev.LBM_ENONFINITE
-    assert "node 5" in ev.lbm_last_error(None)
+    for r in (rho, np.ones(16)):
+        with pytest.raises(ev.LBMError) as e:
+            ev.lbm_init(p, r, np.zeros((2, 16)), np.ones(16))
+        assert e.value.code == ev.LBM_ECUDA
+        assert ev.lbm_last_error(None)
 
 
 def test_bounds_check_query():
