@@ -434,3 +434,33 @@ def test_rollout_fallback_paths():
             e2.copy_(tmp)
         torch.cuda.synchronize()
         assert torch.equal(d2, e2)
+
+
+def test_rollout_interface_indicator():
+    """The interface-position indicator counts, per domain, the nodes whose phase (rho
+    above / below rho_mid) differs between the proposal and the current fields: a window
+    is accepted at a threshold of the largest count and falls back just below it (the
+    count taken here on the host from the same proposal)."""
+    Bn, n, steps = 2, 64, 10
+    F0 = droplet_batch(Bn, n, 5)
+    Mb = n * n
+    p = ev.lbm_params.make(nx=n, ny=n, nz=Bn, eos=ev.LBM_EOS_CS, a=0.1, b=4.0, kappa=0.116, tau=0.3,
+                           precision=ev.LBM_FP32)
+    rho_mid = float(0.5 * (F0[0].max() + F0[0].min()))
+    with S.Surrogate(n, n, seed=9) as m, ev.Lattice(p, F0[0], F0[1:3], F0[3]) as lb:
+        m.set_norm(NORM[0], NORM[1], NORM[2] * 4.0)         # larger increments than the default scale
+        d = torch.tensor(F0, dtype=torch.float32, device=dev).contiguous()
+        prop = torch.empty_like(d)
+        m.infer(d.data_ptr(), prop.data_ptr(), Bn)
+        torch.cuda.synchronize()
+        a = (d[0].cpu().numpy() > rho_mid).reshape(Bn, Mb)
+        b = (prop[0].cpu().numpy() > rho_mid).reshape(Bn, Mb)
+        fmax = int((a != b).sum(axis=1).max())
+        for shift, want_fallbacks in (((fmax + 0.25) / Mb, 0), ((fmax - 0.5) / Mb, 1)):
+            dd = d.clone()
+            torch.cuda.synchronize()
+            nfb, used = m.rollout(lb.ctx, dd.data_ptr(), Bn, 1, steps, rho_mid, 1e30, 1e30, False, shift)
+            assert nfb == want_fallbacks, (fmax, shift, nfb)
+            if want_fallbacks == 0:
+                assert torch.equal(dd, prop)
+    print(f"\nlargest phase-flip count of the proposal: {fmax} of {Mb} nodes")
