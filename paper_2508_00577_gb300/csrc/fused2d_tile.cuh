@@ -1,7 +1,8 @@
 // Tile body of the fused single-pass D2Q9 step of the Enskog-Vlasov lattice
-// Boltzmann model (Karlin & Hosseini, arXiv 2508.00577), FP32 arithmetic and
-// storage; used by the per-step kernel (fused2d.cu) and the persistent batched
-// driver (batch.cu).
+// Boltzmann model (Karlin & Hosseini, arXiv 2508.00577), FP32 arithmetic with FP32
+// storage or FP16 / BF16 deviation storage (dev16.cuh); used by the per-step kernels
+// (fused2d_launch.cuh, instantiated in fused2d.cu and fused2d16.cu) and, FP32 only, the
+// persistent batched driver (batch.cu).
 //
 // One kernel does the whole step of Eq. (pre_LBM): pull streaming, raw moments,
 // the Enskog-gauge force F = grad(a rho^2) + kappa rho grad(lap rho) in
