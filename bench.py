@@ -41,7 +41,7 @@ BYTES_PER_LU = 2 * 9 * 2 * 4          # D2Q9, f and g, read + write, FP32
 # shape (W, H) of the fused kernel (H = -1: the balanced grid, k_fused2d_bal), from one ncu
 # capture each (profiles/fused2d_d2q9_thermal_fp32.md); a shape without a capture, or a
 # changed kernel, reports None.
-MEASURED_TRAFFIC_BYTES = {(128, 256): 1.3353e9, (128, -1): 1.3384e9}
+MEASURED_TRAFFIC_BYTES = {(128, 256): 1.3342e9, (128, -1): 1.3384e9}
 # Floating-point operations per lattice update of the FP64 oracle's plain form of the
 # step (every stencil and equilibrium product summed over all Q velocities), counted by
 # running the oracle's source with a counting number type; tests/test_oracle_flops.py
