@@ -52,7 +52,7 @@ FP32_LANES = 152 * 128
 # DRAM bytes (read + write) of one step of the 512-domain ensemble per work-item shape,
 # from one ncu capture of a one-step launch of k_batch (5.949 GB algorithmic;
 # profiles/batch_ensemble_d2q9_fp32.md); None for other shapes or when the kernel changes.
-ENSEMBLE_TRAFFIC_BYTES_PER_STEP = {(128, 256): 6.0412e9, (128, 512): 6.0011e9}
+ENSEMBLE_TRAFFIC_BYTES_PER_STEP = {(128, 256): 6.0400e9, (128, 512): 6.0011e9}
 WORKLOAD = "droplet Laplace sweep: 9 x 1024^2 D2Q9 thermal, FP32"
 
 
