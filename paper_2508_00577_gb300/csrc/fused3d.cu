@@ -19,7 +19,8 @@
 //   D: collide (q-3)               u, T fields of q-4..q-2, the tile's pulled f from
 //                                  the TMEM stash stage A wrote 3 planes ago, pulled g
 //                                  again (L2 hits: stage C read them 1 plane ago; FP32
-//                                  loads them at the start of stage C)
+//                                  loads them at the start of stage C; 16-bit storage
+//                                  takes stage C's decoded g from a TMEM stash)
 // Shared fields live in 3-deep plane rings sized to the region that reads them;
 // centre values pass from C to D through a one-plane per-thread slot (stage C takes
 // the tile column a thread collides in D first, and reads the slot before rewriting
@@ -56,6 +57,7 @@ template <int TX_, int TY_> struct Geo {
     static constexpr int O_PF = O_PI + 6 * SB;    // [3 planes][3 comps][SC]  partial forces, per stage-C column
     static constexpr int O_CF = O_PF + 9 * SC;    // [3 planes][7][SC]  ux uy uz qx qy qz wq
     static constexpr int O_CEN = O_CF + 21 * SC;  // [7][NT]  rho Fx Fy Fz RT theta0 gamma0 (one plane)
+    static constexpr int NR = 2 * WC + 2 * TY;    // stage C's ring columns (the tile + 1 outside the tile)
     static constexpr size_t SMEM_BYTES = sizeof(float) * (O_CEN + 7 * NT);
 };
 // Tile shape per storage type.  FP32: 32 x 8, so that a warp's load of one population is
@@ -129,6 +131,56 @@ __device__ __forceinline__ void tm_ld9(uint32_t ta, int kz, float v[9])
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                    "=r"(r[8])
                  : "r"(ta + 8u * (uint32_t)kz), "r"(ta + 24u + (uint32_t)kz) : "memory");
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Thermal kernel with 16-bit storage: stage D would otherwise decode the tile's 27 g a
+// second time (stage C decoded them one iteration earlier for the energy), and a g costs
+// about three times an f to decode.  The thread's 128 columns then hold two plane slots of
+// stage C's decoded g (plane mod 2, columns 32 s + [0, 27) in the layout above) and four
+// plane slots of stage A's decoded f of the layers c_z = -1, 0 only (kz = 0, 1): population
+// 9 kz + j at 64 + 16 s + 8 kz + j for j < 8 and at gs_f8(s) + kz for j = 8 (columns 28-31
+// and 60-63, free in the g slots).  Stage D decodes the f of the third layer again.
+constexpr uint32_t GS_F = 64;
+__device__ __forceinline__ uint32_t gs_f8(int s) { return (uint32_t)((s < 2 ? 28 : 56) + 2 * s); }
+
+// Layer kz of nine values into a slot of the 27-value layout (completed by tm_wait_st).
+__device__ __forceinline__ void tm_st9(uint32_t ta, int kz, const float v[9])
+{
+    __syncwarp();
+#define R_(k) "r"(__float_as_uint(v[k]))
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(ta + 8u * (uint32_t)kz), R_(0), R_(1), R_(2), R_(3), R_(4), R_(5), R_(6), R_(7) : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(ta + 24u + (uint32_t)kz), R_(8) : "memory");
+#undef R_
+}
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// The f of layers kz = 0, 1 of v[27] into f slot s.
+__device__ __forceinline__ void tm_st18(uint32_t tb, int s, const float v[27])
+{
+    __syncwarp();
+#define R_(k) "r"(__float_as_uint(v[k]))
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(tb + GS_F + 16u * (uint32_t)s), R_(0), R_(1), R_(2), R_(3), R_(4), R_(5), R_(6), R_(7), R_(9),
+                 R_(10), R_(11), R_(12), R_(13), R_(14), R_(15), R_(16) : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(tb + gs_f8(s)), R_(8), R_(17) : "memory");
+#undef R_
+    tm_wait_st();
+}
+// Layer kz (0 or 1) of f slot s, waited for before it is used.
+__device__ __forceinline__ void tm_ld9f(uint32_t tb, int s, int kz, float v[9])
+{
+    __syncwarp();
+    uint32_t r[9];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%9];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%8}, [%10];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8])
+                 : "r"(tb + GS_F + 16u * (uint32_t)s + 8u * (uint32_t)kz), "r"(tb + gs_f8(s) + (uint32_t)kz)
+                 : "memory");
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[k] = __uint_as_float(r[k]);
 }
@@ -218,12 +270,13 @@ __device__ __forceinline__ void psi3_poly(float A0, float A1, float A2, float ou
 }
 
 // Two resident CTAs per SM (128 registers per thread).  The thermal kernel with 16-bit
-// storage spills ~190 B per thread at that budget; one CTA per SM with 245 registers and
-// no spill was measured slower (2.11 against 2.49 GLUPS at 256^3).
+// storage spills ~40 B per thread at that budget; one CTA per SM with 245 registers and
+// no spill was measured slower (2.11 against 2.49 GLUPS at 256^3, an earlier form).
 template <bool THERMAL, typename S>
 __global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3d(const Args<S> A)
 {
     constexpr bool DEV = Store<S>::dev;
+    constexpr bool GST = DEV && THERMAL;                  // the g-stash layout of the TMEM columns
     using G = typename TileOf<S>::G;
     constexpr int TX = G::TX, TY = G::TY, NT = G::NT, WA = G::WA, WB = G::WB, WC = G::WC;
     constexpr uint32_t TM_COLS = NT;                      // 128 columns per warp of a lane quarter
@@ -250,15 +303,17 @@ __global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3
     };
     auto colB = [&](int k, int &cx, int &cy) { const int c = t + k * NT; cx = c % WB - 2; cy = c / WB - 2; return c < SB; };
     // Stage C: first the tile's own column of this thread (the one it collides in stage D,
-    // so the centre values stay thread-private), then the 68 ring columns on threads 0..67.
-    auto colC = [&](int k, int &cx, int &cy) {
-        if (k == 0) { cx = t % TX; cy = t / TX; return true; }
-        const int r = t;
+    // so the centre values stay thread-private), then the NR ring columns on threads 0..NR-1.
+    auto ringC = [&](int r, int &cx, int &cy) {
         if (r < WC) { cx = r - 1; cy = -1; }
         else if (r < 2 * WC) { cx = r - WC - 1; cy = TY; }
         else if (r < 2 * WC + TY) { cx = -1; cy = r - 2 * WC; }
         else { cx = TX; cy = r - 2 * WC - TY; }
-        return r < 2 * WC + 2 * TY;
+    };
+    auto colC = [&](int k, int &cx, int &cy) {
+        if (k == 0) { cx = t % TX; cy = t / TX; return true; }
+        ringC(t, cx, cy);
+        return t < G::NR;
     };
     auto sa = [](int cx, int cy) { return (cy + 3) * WA + (cx + 3); };
     auto sb = [](int cx, int cy) { return (cy + 2) * WB + (cx + 2); };
@@ -303,7 +358,10 @@ __global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3
                     if (cyi(i) == 1) jy += h; else if (cyi(i) == -1) jy -= h;
                     if (czi(i) == 1) jz += h; else if (czi(i) == -1) jz -= h;
                 }
-                if (k == 0) tm_st27(tmt + (uint32_t)(((q + 4) & 3) * TM_SLOT), hv);     // all threads: slot of plane q
+                if (k == 0) {                                 // all threads: slot of plane q
+                    if constexpr (GST) tm_st18(tmt, (q + 4) & 3, hv);
+                    else tm_st27(tmt + (uint32_t)(((q + 4) & 3) * TM_SLOT), hv);
+                }
                 if (in_bounds(sa(cx, cy), SA)) RHO[s0 * SA + sa(cx, cy)] = rho;
                 if (cx >= -1 && cx <= TX && cy >= -1 && cy <= TY && in_bounds(sc(cx, cy), SC)) {
                     float *jr = J + s0 * 3 * SC + sc(cx, cy);
@@ -383,6 +441,29 @@ __global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3
             for (int k = 0; k < 2; ++k) {
                 int cx, cy;
                 if (!colC(k, cx, cy)) continue;
+                float Gam = 0.f;                          // sum of the pulled g (thermal)
+                if constexpr (GST) {
+                    // The tile column's g of plane q-2, summed and stashed for stage D of the
+                    // next iteration (warp-collective stores: before any per-thread branch).
+                    if (k == 0 && runC) {
+                        const Cell c = cell_of(x0 + cx, y0 + cy, nx, ny);
+                        const uint32_t tg = tmt + (uint32_t)(((q + 2) & 1) * TM_SLOT);
+#pragma unroll
+                        for (int kz = 0; kz < 3; ++kz) {
+                            float v9[9];
+#pragma unroll
+                            for (int j = 0; j < 9; ++j) {
+                                const int i = 9 * kz + j;
+                                const unsigned si = src_of(i, c, zo, N);
+                                v9[j] = decode_g<27>(cxi(i), cyi(i), czi(i), ldrec(A.Rin, si - i * N, N),
+                                                     ldc(A.g, si, 27ull * N));
+                                Gam += v9[j];             // in index order, as the ring columns sum
+                            }
+                            tm_st9(tg, kz, v9);
+                        }
+                        tm_wait_st();
+                    }
+                }
                 const int b0 = sb(cx, cy);
                 const int pc = k == 0 ? t : NT + t;       // this column's partial-force slot
                 if (!(in_bounds(b0 - WB - 1, SB) && in_bounds(b0 + WB + 1, SB) && in_bounds(sc(cx, cy), SC) &&
@@ -427,14 +508,15 @@ __global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3
                 const float ux = (jr[0] + 0.5f * Fx) * ir, uy = (jr[SC] + 0.5f * Fy) * ir, uz = (jr[2 * SC] + 0.5f * Fz) * ir;
                 float RT;
                 if (THERMAL) {
-                    const Cell c = cell_of(x0 + cx, y0 + cy, nx, ny);
-                    float Gam = 0.f;
+                    if (!(GST && k == 0)) {
+                        const Cell c = cell_of(x0 + cx, y0 + cy, nx, ny);
 #pragma unroll
-                    for (int i = 0; i < 27; ++i) {
-                        const unsigned si = src_of(i, c, zo, N);
-                        float h = ldc(A.g, si, 27ull * N);
-                        if constexpr (DEV) h = decode_g<27>(cxi(i), cyi(i), czi(i), ldrec(A.Rin, si - i * N, N), h);
-                        Gam += h;
+                        for (int i = 0; i < 27; ++i) {
+                            const unsigned si = src_of(i, c, zo, N);
+                            float h = ldc(A.g, si, 27ull * N);
+                            if constexpr (DEV) h = decode_g<27>(cxi(i), cyi(i), czi(i), ldrec(A.Rin, si - i * N, N), h);
+                            Gam += h;
+                        }
                     }
                     const float E = (Gam + 0.5f * (ux * Fx + uy * Fy + uz * Fz)) * ir;
                     RT = (2.f / 3.f) * (E - 0.5f * (ux * ux + uy * uy + uz * uz));
@@ -579,6 +661,7 @@ __global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3
                 hq[2] = 0.5f * qz;
             }
             auto sel3 = [](const float v[3], int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); };
+            auto sel3u = [](const unsigned v[3], int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); };
             // One c_z layer of nine populations per pass; with 16-bit storage the passes are
             // not unrolled, which bounds how many source records the compiler keeps in flight.
 #pragma unroll(DEV ? 1 : 3)
@@ -594,10 +677,48 @@ __global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3
                 }
                 const float iwz = cz ? 6.f : 1.5f;
                 float hf9[9];                                 // pulled f of this layer (stage A's stash)
-                tm_ld9(tmp, kz, hf9);
-                if constexpr (DEV && THERMAL) {
-                    // 16-bit thermal: f and g of each source node in one pass, sharing the
-                    // source's record and its P factors (Eqs. feq, geq at the record).
+                if constexpr (GST) {
+                    // 16-bit thermal: the pulled g of this layer from stage C's stash, the f of
+                    // layers c_z = -1, 0 from stage A's, those of c_z = +1 decoded again from
+                    // their source records (Eq. feq at the record).
+                    // f first (its output written before the g are loaded: fewer live registers)
+                    auto emit_f = [&](int cx, float Ey, float Sly, float iwxy, unsigned i, float hf) {
+                        const float feq = ref_f_of(rex[cx + 1], Ey);
+                        const float vf = kh * hf + keq * feq + kst * (rsx[cx + 1] * Sly);
+                        if (act) stc(A.fo, i * N + out, 27ull * N, (vf - feq) * (inv_f * (iwxy * iwz)));
+                    };
+                    if (kz < 2) {
+                        tm_ld9f(tmt, (p + 4) & 3, kz, hf9);
+#pragma unroll
+                        for (int j = 0; j < 9; ++j) {
+                            const int cx = j % 3 - 1, cy = j / 3 - 1;
+                            emit_f(cx, E[cy + 1], Sl[cy + 1], (cx ? 6.f : 1.5f) * (cy ? 6.f : 1.5f),
+                                   (unsigned)j + 9u * (unsigned)kz, hf9[j]);
+                        }
+                    } else {
+                        // c_z = +1 (sources in plane p - 1): decoded as decode_f does, one row of
+                        // three sources at a time (bounds the records in flight)
+#pragma unroll 1
+                        for (int cy = -1; cy <= 1; ++cy) {
+                            const float Ey = sel3(E, cy + 1), Sly = sel3(Sl, cy + 1);
+                            const unsigned yo = sel3u(cD.yo, 1 - cy);
+#pragma unroll
+                            for (int cx = -1; cx <= 1; ++cx) {
+                                const unsigned sn = zo[0] + yo + cD.xo[1 - cx];
+                                const unsigned i = 18u + 3u * (unsigned)(cy + 1) + (unsigned)(cx + 1);
+                                const Ref16 r = ldrec(A.Rin, sn, N);
+                                const float rPx = __fmul_rn(r.rho, refP(cx, r.u[0], r.th));
+                                const float PyPz = __fmul_rn(refP(cy, r.u[1], r.th), refP(1, r.u[2], r.th));
+                                const float w = cy ? wgt16<27>(cx, 1, 1) : wgt16<27>(cx, 0, 1);
+                                const float hf = __fmaf_rn(__fmul_rn(w, r.rho), ldc(A.f, i * N + sn, 27ull * N),
+                                                           ref_f_of(rPx, PyPz));
+                                emit_f(cx, Ey, Sly, (cx ? 6.f : 1.5f) * (cy ? 6.f : 1.5f), i, hf);
+                            }
+                        }
+                    }
+                    // then the g of this layer, from stage C's stash
+                    float hg9[9];
+                    tm_ld9(tmt + (uint32_t)(((p + 4) & 1) * TM_SLOT), kz, hg9);
                     const float Szk = sel3(Sz, kz), pzk = sel3(pz, kz), Tzk = sel3(Tz, kz);
                     float C[3], P[3], Dd[3];
 #pragma unroll
@@ -609,34 +730,18 @@ __global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3
 #pragma unroll
                     for (int j = 0; j < 9; ++j) {
                         const int cx = j % 3 - 1, cy = j / 3 - 1;
-                        const unsigned sn = zs + cD.yo[1 - cy] + cD.xo[1 - cx];
                         const unsigned i = (unsigned)j + 9u * (unsigned)kz;
-                        const float hf = hf9[j];
-                        float hg = ldc(A.g, i * N + sn, 27ull * N);
-                        {
-                            const Ref16 r = ldrec(A.Rin, sn, N);
-                            const float Px = refP(cx, r.u[0], r.th), Py = refP(cy, r.u[1], r.th);
-                            const float Pz = refP(cz, r.u[2], r.th);
-                            const float rPx = __fmul_rn(r.rho, Px), PyPz = __fmul_rn(Py, Pz);
-                            const float w = cz ? wgt16<27>(cx, cy, 1) : wgt16<27>(cx, cy, 0);
-                            const float wr = __fmul_rn(w, r.rho);
-                            const float ref = ref_g_of(ref_A(r.rho, r.e, Px, refS(cx, r.u[0], r.th)), rPx, PyPz,
-                                                       ref_D(Py, refS(cy, r.u[1], r.th), Pz, refS(cz, r.u[2], r.th)));
-                            hg = __fmaf_rn(__fmul_rn(wr, r.e), hg, ref);
-                        }
                         const float iw = (cx ? 6.f : 1.5f) * (cy ? 6.f : 1.5f) * iwz;
-                        const float feq = ref_f_of(rex[cx + 1], E[cy + 1]);
-                        const float vf = kh * hf + keq * feq + kst * (rsx[cx + 1] * Sl[cy + 1]);
-                        if (act) stc(A.fo, i * N + out, 27ull * N, (vf - feq) * (inv_f * iw));
                         const float geq = ref_g_of(Ag[cx + 1], rex[cx + 1], E[cy + 1], C[cy + 1]);
                         float gst = As[cx + 1] * P[cy + 1] + rpx[cx + 1] * Dd[cy + 1];
                         if (cx != 0 && cy == 0) gst += cz == 0 ? cx * hq[0] : 0.f;
                         if (cx == 0 && cy != 0) gst += cz == 0 ? cy * hq[1] : 0.f;
                         if (cx == 0 && cy == 0) gst += float(cz) * hq[2];
-                        const float vg = kh * hg + keq * geq + kst * gst;
+                        const float vg = kh * hg9[j] + keq * geq + kst * gst;
                         if (act) stc(A.go, i * N + out, 27ull * N, (vg - geq) * (inv_g * iw));
                     }
                 } else {
+                    tm_ld9(tmp, kz, hf9);
 #pragma unroll
                     for (int j = 0; j < 9; ++j) {
                         const int cx = j % 3 - 1, cy = j / 3 - 1;
