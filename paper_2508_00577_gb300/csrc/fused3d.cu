@@ -8,8 +8,9 @@
 // geq, gstar, g_corr) and the collision of Eq. (pre_LBM).
 //
 // Work decomposition (2.5-D z-marching).  A CTA owns a tile of 256 (x, y) output columns
-// (32 x 8 with FP32 storage, 16 x 16 with 16-bit storage, see TileOf) of one z-chunk and
-// walks its planes one per iteration; four stages lag by one plane because the
+// (32 x 8 with FP32 storage, 16 x 16 with 16-bit storage, see TileOf) of one z-chunk (the
+// last chunks shorter, so that the grid's last wave is short: step_t) and walks its
+// planes one per iteration; four stages lag by one plane because the
 // collision needs u and T within radius 1,
 // hence F within radius 1, hence the Korteweg stress within radius 2, hence rho
 // within radius 3:
@@ -67,6 +68,8 @@ template <int TX_, int TY_> struct Geo {
 template <typename S> struct TileOf { using G = Geo<16, 16>; };
 template <> struct TileOf<float> { using G = Geo<32, 8>; };
 
+constexpr int kMaxTail = 8, kMinTail = 8;
+
 template <typename S> struct Args {
     const S *f, *g;
     S *fo, *go;
@@ -74,6 +77,10 @@ template <typename S> struct Args {
     float *Rout;                                  // reference records written
     const float *RT_iso;
     int nx, ny, nz, HZ;
+    // z-chunks: nfull chunks of HZ planes, then ntail shorter ones at offsets tail[] from
+    // nfull * HZ (tail[ntail] = the planes left), so that the last CTAs to run are short.
+    int nfull, ntail;
+    int tail[kMaxTail + 1];
     unsigned N;
     int eos;
     float a, b, kappa, lambda, c_eq, c_star;
@@ -284,8 +291,10 @@ __global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3
     extern __shared__ float sm[];
     const int t = threadIdx.x;
     const int nx = A.nx, ny = A.ny, nz = A.nz;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * A.HZ;
-    const int zend = min(z0 + A.HZ, nz);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int ch = (int)blockIdx.z, zt = ch - A.nfull, zb = A.nfull * A.HZ;
+    const int z0 = zt < 0 ? ch * A.HZ : zb + A.tail[zt];
+    const int zend = zt < 0 ? z0 + A.HZ : zb + A.tail[zt + 1];
     const unsigned N = A.N;
     const float a = A.a, b = A.b, kappa = A.kappa, lambda = A.lambda;
 
@@ -800,7 +809,7 @@ cudaError_t launch(const Args<S> &A, cudaStream_t st)
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    const dim3 grid((A.nx + G::TX - 1) / G::TX, (A.ny + G::TY - 1) / G::TY, (A.nz + A.HZ - 1) / A.HZ);
+    const dim3 grid((A.nx + G::TX - 1) / G::TX, (A.ny + G::TY - 1) / G::TY, A.nfull + A.ntail);
     k_fused3d<THERMAL, S><<<grid, G::NT, G::SMEM_BYTES, st>>>(A);
     return cudaGetLastError();
 }
@@ -829,6 +838,27 @@ cudaError_t step_t(const KParams &p, const void *f, const void *g, void *fo, voi
     A.c_eq = float(p.c_eq);
     A.c_star = float(p.c_star);
     A.HZ = p.tile_h > 0 ? p.tile_h : (p.nz < 64 ? p.nz : 64);
+    // Chunks of HZ planes while more than 2 HZ remain, then the rest halved down to
+    // kMinTail planes: CTAs start in chunk order, so the short chunks fill the last wave.
+    // Chunks of at most 2 kMinTail planes are all HZ (the last one what is left).
+    const int H = A.HZ < p.nz ? A.HZ : p.nz;
+    A.HZ = H;
+    A.tail[0] = 0;
+    if (H > 2 * kMinTail) {
+        A.nfull = p.nz > 2 * H ? (p.nz - 2 * H + H - 1) / H : 0;
+        const int R = p.nz - A.nfull * H;
+        int off = 0, k = 0;
+        while (off < R) {
+            const int rem = R - off;
+            off += (rem > 2 * kMinTail && k < kMaxTail - 1) ? (rem + 1) / 2 : rem;
+            A.tail[++k] = off;
+        }
+        A.ntail = k;
+    } else {
+        A.nfull = (p.nz - 1) / H;
+        A.tail[1] = p.nz - A.nfull * H;
+        A.ntail = 1;
+    }
     return p.thermal ? launch<true, S>(A, st) : launch<false, S>(A, st);
 }
 
