@@ -1,8 +1,8 @@
 """Bounds-checked build (libevlbm_bc.so, -DEVLBM_BOUNDS_CHECK): the fused kernels compare
 every global and shared-memory index they use with the extent of its array, count an
 index out of range and skip the access.  Ragged lattices through every launch shape of
-the D2Q9 kernel, z-chunks of the D3Q27 kernel that do not divide nz (FP32 and 16-bit
-storage), 16-bit storage through the D2Q9 kernel, the D2Q9 kernel's wall columns on a
+the D2Q9 kernel, z-chunks of the D3Q27 kernel that do not divide nz or end on shorter
+ones (FP32 and 16-bit storage), 16-bit storage through the D2Q9 kernel, the D2Q9 kernel's wall columns on a
 ragged strip, and an ensemble of small
 uneven domains must meet no such index, and the checked library must still agree with
 the FP64 oracle (1e-5; 1e-3 for 16-bit storage).  The checked library runs in a child process (EVLBM_LIBRARY)."""
@@ -46,7 +46,7 @@ for (nx, ny, nz) in [(7, 5, 1), (130, 70, 2), (257, 33, 1), (1, 1, 1)]:
             o = oracle.State(oracle.Params(Q=9, nx=nx, ny=ny, nz=nz, eos=E.CS, a=A, b=B, kappa=kappa, tau=0.3), *f)
             o.step(5)
             check(f"d2q9 {nx}x{ny}x{nz} W{W} H{H}", o, rho)
-for (nx, ny, nz, hz) in [(20, 18, 11, 4), (33, 16, 7, 3), (5, 3, 4, 1), (17, 17, 17, 64)]:
+for (nx, ny, nz, hz) in [(20, 18, 11, 4), (33, 16, 7, 3), (5, 3, 4, 1), (17, 17, 17, 64), (20, 18, 50, 17)]:
     f = inputs.spinodal_noise(nx, ny, nz, 0.5 * (s1 + s2), RT, amplitude=0.05, D=3)
     p = ev.lbm_params.make(lattice=ev.LBM_D3Q27, nx=nx, ny=ny, nz=nz, eos=ev.LBM_EOS_CS, a=A, b=B, kappa=kappa,
                            precision=ev.LBM_FP32)
@@ -57,7 +57,7 @@ for (nx, ny, nz, hz) in [(20, 18, 11, 4), (33, 16, 7, 3), (5, 3, 4, 1), (17, 17,
     o = oracle.State(oracle.Params(Q=27, nx=nx, ny=ny, nz=nz, eos=E.CS, a=A, b=B, kappa=kappa, tau=0.3), *f)
     o.step(4)
     check(f"d3q27 {nx}x{ny}x{nz} z-chunk {hz}", o, rho)
-    if hz in (4, 1):
+    if hz in (4, 1, 17):
         # 16-bit deviation storage through the same fused kernel (its TMEM stash included)
         for prec, tag in ((ev.LBM_FP16_DEV, "fp16"), (ev.LBM_BF16_DEV, "bf16")):
             p16 = ev.lbm_params.make(lattice=ev.LBM_D3Q27, nx=nx, ny=ny, nz=nz, eos=ev.LBM_EOS_CS, a=A, b=B,
@@ -129,7 +129,7 @@ def test_checked_library_meets_no_out_of_range_index():
     assert r.returncode == 0, r.stderr[-3000:]
     res = json.loads(r.stdout.split("RESULT ", 1)[1])
     assert res["start"] == 0
-    assert len(res["cases"]) == 4 * 4 * 4 + 4 + 2 * 2 + 2 * 2 * 2 + 2 + 3
+    assert len(res["cases"]) == 4 * 4 * 4 + 5 + 3 * 2 + 2 * 2 * 2 + 2 + 3
     for name, err, oob in res["cases"]:
         assert oob == 0, f"{name}: {oob} out-of-range indices"
         assert err <= (1e-3 if ("fp16" in name or "bf16" in name) else 1e-5), f"{name}: max rel rho error {err}"

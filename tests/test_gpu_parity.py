@@ -165,12 +165,13 @@ def test_fp32_d2q9(nx, ny, nz):
 
 @pytest.mark.parametrize("thermal", [1, 0])
 @pytest.mark.parametrize("nx,ny,nz,hz", [(20, 18, 11, 0), (33, 16, 7, 4), (16, 16, 16, 5), (5, 3, 4, 0),
-                                         (40, 35, 9, 3)])
+                                         (40, 35, 9, 3), (20, 18, 70, 20), (12, 10, 50, 17)])
 def test_fp32_d3q27(nx, ny, nz, hz, thermal):
     """FP32 D3Q27 (fused single-pass kernel): max |d rho|/rho <= 1e-5 over 10 steps of a
     spinodal state with 5 % density noise.  Edges that are not multiples of the 32 x 8
     tile (16 x 16 with 16-bit storage), odd plane counts, z-chunks that do not divide nz (hz; 0 = default chunk) and a
-    lattice smaller than one tile."""
+    lattice smaller than one tile.  Chunks above 16 planes end on shorter ones: 70 planes
+    at hz 20 run as 20, 20, 15, 15 and 50 at hz 17 as 17, 17, 16."""
     _, Tc = E.critical_point(E.CS, A, B)
     RT = 0.85 * Tc
     s1, s2 = E.spinodal(E.CS, A, B, RT)
@@ -184,6 +185,30 @@ def test_fp32_d3q27(nx, ny, nz, hz, thermal):
         o.step(10)
         g.step(10)
         assert_fields(o, g, 1e-5)
+
+
+@pytest.mark.parametrize("precision", [ev.LBM_FP16_DEV, ev.LBM_BF16_DEV])
+@pytest.mark.parametrize("nx,ny,nz,hz", [(20, 18, 11, 4), (33, 17, 50, 17), (7, 5, 3, 0)])
+def test_reduced_precision_d3q27(precision, nx, ny, nz, hz):
+    """16-bit deviation storage through the fused D3Q27 kernel (one launch per step, the
+    decoded f and g stashed in tensor memory): rho and T within 1e-3 relative, u within
+    1e-4 of the FP64 oracle after 10 thermal steps of a spinodal state with 5 % density
+    noise, on edges that are not multiples of the 16 x 16 tile, uniform z-chunks that do
+    not divide nz, chunks ending on shorter ones (50 planes at hz 17: 17, 17, 16) and a
+    lattice smaller than one tile."""
+    _, Tc = E.critical_point(E.CS, A, B)
+    RT = 0.85 * Tc
+    s1, s2 = E.spinodal(E.CS, A, B, RT)
+    kappa = E.kappa_for_width(E.CS, A, B, RT, 4.0)
+    fields = inputs.spinodal_noise(nx, ny, nz, 0.5 * (s1 + s2), RT, amplitude=0.05, D=3)
+    o, g = pair(27, nx, ny, nz, fields, kappa, precision)
+    with g:
+        if hz:
+            ev.lbm_set_tile(g.ctx, 0, hz)
+        assert ev.lbm_launches_per_step(g.ctx) == 1
+        o.step(10)
+        g.step(10)
+        assert_fields(o, g, 1e-3)
 
 
 @pytest.mark.parametrize("lam", [0.5, 2.0])
