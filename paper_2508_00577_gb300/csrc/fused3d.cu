@@ -7,8 +7,8 @@
 // Phi, Phi', q' (Eqs. correction_u/gamma/q), the equilibria (Eqs. feq, f_star,
 // geq, gstar, g_corr) and the collision of Eq. (pre_LBM).
 //
-// Work decomposition (2.5-D z-marching).  A CTA owns a tile of 256 (x, y) output columns
-// (32 x 8 with FP32 storage, 16 x 16 with 16-bit storage, see TileOf) of one z-chunk (the
+// Work decomposition (2.5-D z-marching).  A CTA owns a tile of (x, y) output columns
+// (32 x 8 with FP32 storage, 32 x 16 with 16-bit storage, see TileOf) of one z-chunk (the
 // last chunks shorter, so that the grid's last wave is short: step_t) and walks its
 // planes one per iteration; four stages lag by one plane because the
 // collision needs u and T within radius 1,
@@ -25,7 +25,7 @@
 // Shared fields live in 3-deep plane rings sized to the region that reads them;
 // centre values pass from C to D through a one-plane per-thread slot (stage C takes
 // the tile column a thread collides in D first, and reads the slot before rewriting
-// it); at 73-77 KB per CTA two CTAs leave the L1 ~85 KB for loads in flight.
+// it); at 77 KB per CTA (32 x 8 tiles) two CTAs leave the L1 ~85 KB for loads in flight.
 //
 // 16-bit storage: every pulled population is rebuilt from its source node's FP32
 // reference record (a 16- and an 8-byte load, L1/L2 hits after the first) and the
@@ -63,9 +63,11 @@ template <int TX_, int TY_> struct Geo {
 };
 // Tile shape per storage type.  FP32: 32 x 8, so that a warp's load of one population is
 // one row of 32 consecutive nodes (16 x 16 tiles load two half rows per warp; 32 x 8 ran
-// 7 % faster despite 10 % more halo columns).  16-bit storage: 16 x 16, whose smaller halo
-// saves more decoding than the wider rows save in loads (32 x 8 was 3.5 % slower).
-template <typename S> struct TileOf { using G = Geo<16, 16>; };
+// 7 % faster despite 10 % more halo columns).  16-bit storage, bound by its decoding:
+// 32 x 16 (512 threads, one CTA per SM), whose halo is the smallest (stage A decodes 1.63
+// columns per tile column against 1.89 for 16 x 16 and 2.08 for 32 x 8; 16 x 16 ran 2.5 %
+// slower, 32 x 8 6 %).
+template <typename S> struct TileOf { using G = Geo<32, 16>; };
 template <> struct TileOf<float> { using G = Geo<32, 8>; };
 
 constexpr int kMaxTail = 8, kMinTail = 8;
@@ -276,9 +278,10 @@ __device__ __forceinline__ void psi3_poly(float A0, float A1, float A2, float ou
     out[2] = 0.5f * (A2 + A1);
 }
 
-// Two resident CTAs per SM (128 registers per thread).  The thermal kernel with 16-bit
-// storage spills ~40 B per thread at that budget; one CTA per SM with 245 registers and
-// no spill was measured slower (2.11 against 2.49 GLUPS at 256^3, an earlier form).
+// 16 warps per SM at 128 registers per thread: two CTAs of 256 threads (FP32) or one of
+// 512 (16-bit storage).  The thermal kernel with 16-bit storage spills ~30 B per thread at
+// that budget; 8 warps per SM with 245 registers and no spill was measured slower (2.11
+// against 2.49 GLUPS at 256^3, an earlier form).
 template <bool THERMAL, typename S>
 __global__ void __launch_bounds__(TileOf<S>::G::NT, TileOf<S>::G::MINB) k_fused3d(const Args<S> A)
 {

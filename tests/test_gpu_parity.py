@@ -169,7 +169,7 @@ def test_fp32_d2q9(nx, ny, nz):
 def test_fp32_d3q27(nx, ny, nz, hz, thermal):
     """FP32 D3Q27 (fused single-pass kernel): max |d rho|/rho <= 1e-5 over 10 steps of a
     spinodal state with 5 % density noise.  Edges that are not multiples of the 32 x 8
-    tile (16 x 16 with 16-bit storage), odd plane counts, z-chunks that do not divide nz (hz; 0 = default chunk) and a
+    tile (32 x 16 with 16-bit storage), odd plane counts, z-chunks that do not divide nz (hz; 0 = default chunk) and a
     lattice smaller than one tile.  Chunks above 16 planes end on shorter ones: 70 planes
     at hz 20 run as 20, 20, 15, 15 and 50 at hz 17 as 17, 17, 16."""
     _, Tc = E.critical_point(E.CS, A, B)
@@ -193,7 +193,7 @@ def test_reduced_precision_d3q27(precision, nx, ny, nz, hz):
     """16-bit deviation storage through the fused D3Q27 kernel (one launch per step, the
     decoded f and g stashed in tensor memory): rho and T within 1e-3 relative, u within
     1e-4 of the FP64 oracle after 10 thermal steps of a spinodal state with 5 % density
-    noise, on edges that are not multiples of the 16 x 16 tile, uniform z-chunks that do
+    noise, on edges that are not multiples of the 32 x 16 tile, uniform z-chunks that do
     not divide nz, chunks ending on shorter ones (50 planes at hz 17: 17, 17, 16) and a
     lattice smaller than one tile."""
     _, Tc = E.critical_point(E.CS, A, B)
@@ -425,9 +425,9 @@ def test_autotune_keeps_state():
             ev.lbm_set_tile(g.ctx, 128, -2)
 
 
-@pytest.mark.parametrize("prec,width", [(ev.LBM_FP32, 32), (ev.LBM_FP16_DEV, 16), (ev.LBM_BF16_DEV, 16)])
+@pytest.mark.parametrize("prec,width", [(ev.LBM_FP32, 32), (ev.LBM_FP16_DEV, 32), (ev.LBM_BF16_DEV, 32)])
 def test_d3q27_tile_shape_per_storage(prec, width):
-    """The D3Q27 kernel's x-y tile is fixed per storage type (32 x 8 for FP32, 16 x 16
+    """The D3Q27 kernel's x-y tile is fixed per storage type (32 x 8 for FP32, 32 x 16
     for 16-bit storage): lbm_set_tile takes tile_w = 0 or that width, lbm_get_tile and
     lbm_autotune report it, and the autotuner leaves the state as it was."""
     _, Tc = E.critical_point(E.CS, A, B)
