@@ -211,9 +211,9 @@ int lbm_launches_per_step(const lbm_ctx *ctx);
 int lbm_set_walls(lbm_ctx *ctx, int enable, const double u_lo[3], const double u_hi[3], double T_w);
 
 /* Launch shape of the fused single-pass kernels.  D3Q27: tile_w = 0 or the kernel's
- * fixed tile width for the storage type (32: tiles of 32 x 8 columns per CTA for FP32;
- * 32: 32 x 16 for FP16/BF16 storage; lbm_get_tile reports it) and tile_h = the z-chunk a
- * CTA marches through (>= 1).  Above 16 planes the last chunks are shorter: chunks of
+ * fixed tile width, 32 (tiles of 32 x 8 columns per CTA for FP32 storage, 32 x 16 for
+ * FP16/BF16; lbm_get_tile reports the width), and tile_h = the z-chunk a CTA marches
+ * through (>= 1).  Above 16 planes the last chunks are shorter: chunks of
  * tile_h while more than 2 tile_h planes remain, then the rest halved down to 8 to 16
  * planes, so that the CTAs that start last (the grid runs in chunk order) end early.
  * D2Q9: strips of
